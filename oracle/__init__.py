@@ -1,0 +1,126 @@
+"""CPU oracle for optimal sum-of-pairs MSA by dynamic programming.
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package. It shares no code with the CUDA path (``libmsadp``).
+
+``msa_oracle.c`` is the plain full-tensor definition of the method (section 2,
+Eq. 1 generalised to 2^k-1 neighbours; section 4 per-cell scoring; section 5.2
+sum-of-pairs columns with gap-gap 0; section 2 traceback). This wrapper only
+marshals arguments and expands the returned move masks into gapped rows.
+
+Every function here is pinned by ``tests/test_oracle_pins.py`` against brute
+force enumeration, textbook Needleman-Wunsch, a closed form, permutation
+invariance and the alignment invariants. The paper's own 6-sequence example
+(section 5.2, optimal SP score -5) is parity unpinned: its sequences are not
+published.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "msa_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libmsa_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, single thread, portable flags)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def load_library(path: str):
+    """ctypes handle on a compiled oracle (the default one, or a planted mutant in tests)."""
+    lib = ctypes.CDLL(path)
+    lib.oracle_msa.restype = ctypes.c_int
+    lib.oracle_msa.argtypes = [
+        ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int,
+        ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = load_library(build())
+    return _lib
+
+
+@dataclasses.dataclass
+class OracleResult:
+    score: int
+    masks: List[int]          # move mask per column, first column first
+    rows: List[str]           # k gapped rows
+    tb: Optional[np.ndarray]  # uint8 tensor, shape (len_i + 1), if requested
+    H: Optional[np.ndarray]   # int64 tensor, if requested
+
+
+def encode(seqs: Sequence[str], alphabet: str) -> np.ndarray:
+    index = {c: i for i, c in enumerate(alphabet)}
+    return np.array([index[c] for s in seqs for c in s], dtype=np.uint8)
+
+
+def expand(seqs: Sequence[str], masks: Sequence[int], gap_char: str = "-") -> List[str]:
+    """Gapped rows from column masks: row i takes its next residue when bit i is set."""
+    pos = [0] * len(seqs)
+    rows = [[] for _ in seqs]
+    for m in masks:
+        for i, s in enumerate(seqs):
+            if (m >> i) & 1:
+                rows[i].append(s[pos[i]])
+                pos[i] += 1
+            else:
+                rows[i].append(gap_char)
+    return ["".join(r) for r in rows]
+
+
+def align_codes(lens: Sequence[int], codes: np.ndarray, A: int, subst: np.ndarray, gap: int,
+                want_tb: bool = False, want_H: bool = False, lib=None):
+    lib = lib or _load()
+    k = len(lens)
+    lens_arr = (ctypes.c_int32 * k)(*[int(n) for n in lens])
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    sub = np.ascontiguousarray(np.asarray(subst, dtype=np.int32).reshape(-1))
+    shape = tuple(int(n) + 1 for n in lens)
+    ncells = int(np.prod(shape, dtype=np.int64))
+    tb = np.empty(shape, dtype=np.uint8) if want_tb else None
+    H = np.empty(shape, dtype=np.int64) if want_H else None
+    masks = np.zeros(max(1, int(sum(lens))), dtype=np.uint8)
+    score = ctypes.c_int64(0)
+    ncols = ctypes.c_int32(0)
+    rc = lib.oracle_msa(
+        k, lens_arr, codes.ctypes.data if codes.size else None, int(A),
+        sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(gap), ctypes.byref(score),
+        tb.ctypes.data if tb is not None else None, H.ctypes.data if H is not None else None,
+        masks.ctypes.data, ctypes.byref(ncols))
+    if rc != 0:
+        raise ValueError(f"oracle_msa failed with {rc} (cells={ncells})")
+    return int(score.value), [int(m) for m in masks[: ncols.value]], tb, H
+
+
+def align(seqs: Sequence[str], alphabet: str, subst, gap: int, want_tb: bool = False,
+          want_H: bool = False, lib=None) -> OracleResult:
+    """Optimal global SP alignment of ``seqs`` (lowest move mask wins ties)."""
+    codes = encode(seqs, alphabet)
+    score, masks, tb, H = align_codes([len(s) for s in seqs], codes, len(alphabet),
+                                      np.asarray(subst), gap, want_tb, want_H, lib)
+    return OracleResult(score, masks, expand(seqs, masks), tb, H)
+
+
+def align_problem(p, want_tb: bool = False, want_H: bool = False) -> OracleResult:
+    return align(p.seqs, p.alphabet, p.subst, p.gap, want_tb, want_H)
