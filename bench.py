@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark: optimal DP-MSA fill + traceback on one GB300 (libmsadp).
+
+One step = the whole hot path over one problem: encode residues + scale the pair
+table, fill the k-dimensional tensor, trace back (hot-path steps a1-a5). The
+default workload is k=3 protein 700/760/800 (427,302,261 cells). Its working set
+(2.1 GB of scores and traceback bytes) is far larger than the 129 MB L2, so no
+L2 flush is needed between steps.
+
+value  : cells/s with inputs resident in HBM (plan execution on device buffers),
+         CUDA events on the launching stream around exactly --steps steps.
+e2e    : cells/s through msa_align() with host buffers (H2D of residues + table,
+         D2H of the result block + masks inside the timed region).
+roofline: the fill kernel against the integer-ALU bound.
+
+--impl reference times the CPU oracle (plain full-tensor DP, one core) on a
+bounded prefix sample of the same workload.
+
+Multi-GPU: the problem does not shard; N ranks run independent replicas.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+
+METRIC = "DP cells/s"
+UNIT = "cells/s"
+SMS_GB300 = 152
+INT32_LANES_PER_SM = 64   # 4 SM sub-partitions x 16 INT32 lanes
+SM_MAX_MHZ_FALLBACK = 2070.0
+
+
+def alg_ops_per_cell(k: int) -> int:
+    """Relaxations of one cell: 2^k - 1 predecessors, each an add and a max."""
+    return 2 * ((1 << k) - 1)
+
+
+def sm_max_mhz() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("sm_max_mhz", SM_MAX_MHZ_FALLBACK))
+    except Exception:
+        return SM_MAX_MHZ_FALLBACK
+
+
+def alu_peak_tiops(sms: int) -> float:
+    return sms * INT32_LANES_PER_SM * sm_max_mhz() * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(self.REASONS, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def sample_prefix(p, target_cells: float):
+    """Prefixes of the workload's sequences, all lengths scaled by one factor."""
+    f = min(1.0, (target_cells / p.cells) ** (1.0 / p.k))
+    lens = [max(1, int(round(n * f))) for n in p.lens]
+    return p.prefix(lens)
+
+
+def time_oracle(p, target_cells: float):
+    import oracle
+    q = sample_prefix(p, target_cells)
+    t0 = time.perf_counter()
+    oracle.align_problem(q)
+    dt = time.perf_counter() - t0
+    return q, dt
+
+
+def kernel_source_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2311_17530_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(f"{kernel}:{workload}")
+    except Exception:
+        return None
+    if not rec or rec.get("source_digest") != kernel_source_digest():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    p = inputs.WORKLOADS[args.workload]()
+    per_step = args.ref_cells
+    for _ in range(args.warmup):
+        time_oracle(p, per_step / 4)
+    times, cells = [], 0
+    q = None
+    for _ in range(args.steps):
+        q, dt = time_oracle(p, per_step)
+        times.append(dt)
+        cells = q.cells
+    total = sum(times)
+    value = cells * args.steps / total
+    sample = f"oracle on prefixes {q.lens} of {p.name} ({cells} cells per step)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": {"workload": p.name, "k": p.k, "lens": p.lens, "cells": p.cells},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gb300(args, rank, world, local):
+    import torch
+
+    from paper_2311_17530_gb300 import msadp
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    p = inputs.WORKLOADS[args.workload]()
+    total_len = sum(p.lens)
+    plan = msadp.Plan(p.k, p.lens, p.alphabet)
+    info = plan.info()
+    d_res, d_sub = msadp.device_inputs(p, dev)
+    d_result, d_masks = msadp.device_outputs(total_len, dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.execute(d_res.data_ptr(), d_sub.data_ptr(), p.gap, d_result.data_ptr(), d_masks.data_ptr(),
+                     stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    score, rows, status = msadp.decode_device_result(d_result, d_masks, p.seqs)
+    if status != 0:
+        raise SystemExit(f"device status {status}")
+    golden = os.path.join(ROOT, "tests", "golden", f"{args.workload}.json")
+    checked = None
+    if os.path.exists(golden):
+        checked = json.load(open(golden))["score"] == score
+        if not checked:
+            raise SystemExit(f"score {score} differs from the stored oracle value")
+
+    msadp.msa_config("timing", 1)
+    try:
+        plan.timings()
+    except msadp.MsaError:
+        pass
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    msadp.msa_config("timing", 0)
+    ms_total = ev0.elapsed_time(ev1)
+    enc_ms, fill_ms, tb_ms = plan.timings()
+    if dist:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+        dist.barrier()
+    ms_step = ms_total / args.steps
+    value = p.cells * world / (ms_step / 1e3)
+
+    # end to end through the public C-ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(max(1, args.warmup)):
+            msadp.msa_align(p.seqs, p.alphabet, p.subst, p.gap)
+        ts = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            s2, _ = msadp.msa_align(p.seqs, p.alphabet, p.subst, p.gap)
+            ts.append(time.perf_counter() - t0)
+            assert s2 == score
+        if dist:
+            t = torch.tensor([sum(ts)], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        else:
+            tot = sum(ts)
+        e2e = {"value": p.cells * world * args.steps / tot, "unit": UNIT,
+               "h2d_bytes_per_step": total_len + p.subst.size * 4,
+               "d2h_bytes_per_step": 16 + total_len, "ms_per_step": 1e3 * tot / args.steps}
+
+    kernel = "fill_tiles" if info.fill_kernel == 1 else "fill_col3"
+    ops = alg_ops_per_cell(p.k) * p.cells
+    achieved = ops / (fill_ms / 1e3) / 1e12
+    peak = alu_peak_tiops(sms)
+    roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TIOP/s",
+                "frac": achieved / peak, "traffic": measured_traffic(args.workload, kernel),
+                "ops_per_cell": alg_ops_per_cell(p.k), "fill_ms": fill_ms, "encode_ms": enc_ms,
+                "traceback_ms": tb_ms,
+                "peak_basis": f"{sms} SMs x {INT32_LANES_PER_SM} INT32 lanes x {sm_max_mhz():.0f} MHz"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        q, dt = time_oracle(p, args.cpu_cells)
+        cpu = {"value": q.cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle on prefixes {q.lens} of {p.name} ({q.cells} cells, {dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": p.name, "k": p.k, "lens": p.lens, "cells": p.cells,
+                       "tiles": int(info.tiles), "fill_kernel": kernel,
+                       "l2": "working set > L2 (no flush)", "parallelism": f"replicas{world}",
+                       "score": score, "score_matches_oracle": checked},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 3 * args.steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="k3_protein", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-cells", type=float, default=1.2e8, help="cells of the cpu_baseline sample")
+    ap.add_argument("--ref-cells", type=float, default=5e7, help="cells per step of --impl reference")
+    args = ap.parse_args()
+    rank, world, local = dist_setup()
+    if args.warmup < 3 and args.impl == "gb300":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_gb300(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

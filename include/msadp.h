@@ -1,0 +1,237 @@
+/*
+ * libmsadp -- optimal multiple sequence alignment by dynamic programming on one
+ * NVIDIA GB300 GPU (sm_103a).
+ *
+ * The method (Helal, El-Gindy, Mullin, Gaeta, "Parallelizing Optimal Multiple
+ * Sequence Alignment by Dynamic Programming"):
+ *   - k sequences span a k-dimensional scoring tensor of shape rho_i = len_i + 1
+ *     (section 3.2: the initial gap character), N = prod rho_i cells (section 2);
+ *   - every cell x != 0 takes the maximum, over its 2^k - 1 lower neighbours
+ *     x - e_m (section 2; Eq. 1 is the k = 2 case), of the neighbour's score plus
+ *     the sum-of-pairs (SP) score of the column the move emits (section 5.2:
+ *     table score for residue/residue, `gap` for residue/gap, 0 for gap/gap);
+ *     the origin scores 0 (section 4);
+ *   - the optimal alignment is traced back from the far corner (section 2).
+ *
+ * Conventions fixed by this library where the paper is silent:
+ *   - global alignment: traceback starts at (len_0, ..., len_{k-1});
+ *   - move mask m: bit i set means sequence i consumes a residue in that column;
+ *   - ties: the lowest move mask wins at every cell, so the returned alignment is
+ *     the optimal one whose reversed column sequence is lexicographically smallest;
+ *   - the substitution table must be symmetric; arithmetic is exact int32.
+ *
+ * All functions return MSA_OK (0) or a negative MSA_E* code; msa_poll may also
+ * return MSA_PENDING. No function aborts the process. A thread-local message for
+ * the last failure is available from msa_last_error().
+ */
+#ifndef MSADP_H
+#define MSADP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSA_OK 0
+#define MSA_PENDING 1
+#define MSA_EINVAL (-1)      /* bad argument: k outside [2,8], NULL pointer, negative length,
+                                residue not in the alphabet, alphabet size outside [1,32] or
+                                with repeated characters, non-symmetric table */
+#define MSA_ETOOBIG (-2)     /* scores could leave the exact int32 range, or the problem
+                                needs more device memory than the configured budget */
+#define MSA_ENOMEM (-3)      /* a device or host allocation failed */
+#define MSA_ECUDA (-4)       /* a CUDA call failed (message in msa_last_error) */
+#define MSA_ETIMEOUT (-5)    /* a device-side dependency wait exceeded its time limit;
+                                the kernel stopped cleanly and the context stays usable */
+#define MSA_EBADHANDLE (-6)  /* unknown, already-consumed or cancelled request handle */
+
+#define MSA_MAX_K 8
+#define MSA_MAX_ALPHABET 32
+
+/* ------------------------------------------------------------------------ */
+/* One alignment, host buffers, synchronous.                                 */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Optimal global SP alignment of k sequences (section 2; section 4; section 5.2).
+ *
+ * k              number of sequences, 2 <= k <= 8
+ * seqs           k pointers to residue strings (not necessarily NUL-terminated)
+ * lens           k lengths, each >= 0 (0 allowed: that row is all gaps)
+ * alphabet       NUL-terminated string of the |S| distinct residue characters
+ *                (case-sensitive), 1 <= |S| <= 32
+ * subst          |S| x |S| int32 substitution scores, row-major, symmetric,
+ *                indexed in alphabet order
+ * gap            score of one residue against a gap (gap against gap scores 0)
+ * out_score      receives the optimal SP score
+ * out_alignment  caller-owned, k * (sum(lens) + 1) bytes: row i starts at
+ *                i * (sum(lens) + 1), holds ncols characters ('-' for gaps) and a
+ *                terminating NUL; every row has the same ncols
+ *
+ * All inputs are read before the call returns; the caller keeps ownership of
+ * every buffer. Work runs on the stream set by msa_set_stream (default: a stream
+ * owned by the library). Thread-safe (calls are serialised internally).
+ */
+int msa_align(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
+              const int32_t *subst, int32_t gap, int32_t *out_score, char *out_alignment);
+
+/* Thread-local description of the last failure in this thread ("" if none). */
+const char *msa_last_error(void);
+
+/* Stream (a cudaStream_t, may be NULL for the legacy default stream) used by
+   msa_align and by the serving loop for launches made from this thread on. */
+int msa_set_stream(void *stream);
+
+/*
+ * Runtime settings (integer values):
+ *   "spin_timeout_ms"   device dependency-wait limit per wait (default 5000)
+ *   "device_budget_mb"  device memory the serving loop may hold (default 16384)
+ *   "max_batch"         problems per batched launch in the serving loop (default 64)
+ *   "use_graphs"        1: the serving loop replays captured CUDA graphs (default 1)
+ *   "batching"          1: serve by continuous batching; 0: one plain launch per
+ *                       request, in arrival order (default 1)
+ *   "fill_kernel"       0: automatic; 1: generic tile kernel; 2: k=3 column kernel
+ *   "timing"            1: msa_plan_execute records per-stage CUDA events (default 0)
+ *   "test_withhold_tile" test hook: the tile with this ticket never publishes its
+ *                       completion, so its dependants time out (default -1: off)
+ */
+int msa_config(const char *key, int64_t value);
+
+/* ------------------------------------------------------------------------ */
+/* Plans: device-resident inputs and outputs, asynchronous.                  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct msa_plan msa_plan;
+
+/* Everything a plan fixed, for callers and tests. */
+typedef struct msa_plan_info {
+    int32_t k;
+    int32_t alphabet_size;
+    int64_t cells;              /* prod(len_i + 1) */
+    int64_t tb_strides[MSA_MAX_K]; /* bytes; traceback tensor index = sum x_i * tb_strides[i]
+                                      (row-major, last axis padded) */
+    int64_t tb_bytes;
+    int64_t workspace_bytes;    /* device bytes the plan owns */
+    int32_t tile_grid[MSA_MAX_K];
+    int32_t tile_extent[MSA_MAX_K];
+    int64_t tiles;
+    int32_t waves;              /* tile hyperplanes (section 3.1, Eq. 2) */
+    int32_t fill_kernel;        /* 1 generic tile kernel, 2 k=3 column kernel */
+    void   *d_tb;               /* device pointer of the uint8 traceback tensor */
+} msa_plan_info;
+
+/* Result block written on the device by msa_plan_execute. */
+typedef struct msa_device_result {
+    int32_t score;   /* optimal SP score */
+    int32_t ncols;   /* alignment columns */
+    int32_t status;  /* MSA_OK, MSA_EINVAL (bad residue / asymmetric table) or MSA_ETIMEOUT */
+    int32_t pad;
+} msa_device_result;
+
+/*
+ * Fix the shape of a problem (k, lens, alphabet) and allocate its device
+ * workspace: residue codes, the scaled pair table, the traceback tensor
+ * (1 byte per cell), the score scratch and the tile schedule (section 3.2:
+ * tiles grouped into waves of equal index sum). Host work plus cudaMalloc.
+ */
+int msa_plan_create(int k, const int32_t *lens, const char *alphabet, msa_plan **out_plan);
+
+/*
+ * Run the whole hot path for one problem on `stream`, without host copies:
+ * encode residues and scale the pair table, fill the tensor, trace back.
+ *
+ * d_residues  device, sum(lens) bytes: the k sequences concatenated in order
+ * d_subst     device, |S|*|S| int32 symmetric table (checked on the device)
+ * gap         residue/gap score
+ * d_result    device msa_device_result
+ * d_masks     device, >= sum(lens) bytes: move mask of every column, LAST column
+ *             first (reverse order), d_result->ncols of them
+ * stream      cudaStream_t or NULL
+ * Returns after launching (MSA_ECUDA if a launch fails). Data errors and
+ * timeouts appear in d_result->status once the stream reaches that point.
+ * A plan runs one execution at a time: launches on one stream serialise.
+ */
+int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_subst, int32_t gap,
+                     msa_device_result *d_result, uint8_t *d_masks, void *stream);
+
+int msa_plan_get_info(const msa_plan *plan, msa_plan_info *out_info);
+int msa_plan_destroy(msa_plan *plan);
+
+/*
+ * Copy the traceback tensor of the last execution to host memory
+ * (info.tb_bytes bytes, layout given by info.tb_strides; the move mask of every
+ * cell, 0 at the origin). Synchronises the plan's last stream. Diagnostic use.
+ */
+int msa_plan_read_tb(msa_plan *plan, void *host_dst, int64_t bytes);
+
+/*
+ * With msa_config("timing", 1), msa_plan_execute records CUDA events around its
+ * three stages on the execution stream (no synchronisation). This returns the
+ * mean stage durations, in milliseconds, over the executions recorded since the
+ * previous call (the last 256 at most): out_ms[0] encode + tables, out_ms[1]
+ * fill, out_ms[2] traceback. Synchronises on the recorded events.
+ */
+int msa_plan_timings(msa_plan *plan, float out_ms[3]);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of independent requests.                     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct msa_request {
+    int32_t k;
+    const char *const *seqs;
+    const int32_t *lens;
+    const char *alphabet;
+    const int32_t *subst;
+    int32_t gap;
+} msa_request;
+
+/*
+ * Queue one alignment (same fields and rules as msa_align). Inputs are copied
+ * before returning. The serving loop admits queued requests into batched
+ * persistent launches while request slots and the device-memory budget allow
+ * (footprint = prod(len_i + 1) traceback bytes plus score scratch), keeps
+ * their tensors on the device, and overlaps new launches with running ones.
+ */
+int msa_submit(const msa_request *req, uint64_t *out_handle);
+
+/*
+ * MSA_PENDING while the request is queued or running; otherwise its final
+ * status, with out_score / out_alignment filled as msa_align does on MSA_OK.
+ * The first call that returns something other than MSA_PENDING releases the
+ * handle. out_alignment needs k * (sum(lens) + 1) bytes.
+ */
+int msa_poll(uint64_t handle, int32_t *out_score, char *out_alignment);
+
+/* Drop a request that has not been polled to completion. */
+int msa_cancel(uint64_t handle);
+
+/* Block until every submitted request has finished (results stay pollable). */
+int msa_drain(void);
+
+/* ------------------------------------------------------------------------ */
+/* Host-only planner queries (no CUDA calls; usable without a GPU).         */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Number of tiles on each wave of a tile grid with extents grid[0..k-1]
+ * (section 3.1 Eq. 2 gives the wave count sum(grid) - k + 1; Eq. 3 the tile count
+ * prod(grid); Tables 1 and 2 list these sizes). out_sizes receives
+ * min(max_waves, waves) values; out_waves the total wave count.
+ */
+int msa_wave_sizes(int k, const int32_t *grid, int64_t *out_sizes, int32_t max_waves,
+                   int32_t *out_waves);
+
+/* The tile extents and tile grid the planner uses for these lengths. */
+int msa_tile_shape(int k, const int32_t *lens, int32_t *out_extent, int32_t *out_grid);
+
+/* Library version string. */
+const char *msa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSADP_H */

@@ -1,0 +1,568 @@
+// libmsadp C-ABI: validation, plans, the synchronous msa_align, settings and
+// the host-only planner queries.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "api_internal.h"
+
+using namespace msadp;
+
+namespace msadp {
+
+thread_local std::string t_err;
+
+int set_error(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+    return set_error(MSA_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+Settings &settings() {
+    static Settings s;
+    return s;
+}
+
+std::mutex &settings_mutex() {
+    static std::mutex m;
+    return m;
+}
+
+static void *g_stream = nullptr;
+static bool g_stream_set = false;
+static cudaStream_t g_own_stream = nullptr;
+
+cudaStream_t library_stream(int *rc) {
+    *rc = MSA_OK;
+    if (g_stream_set) return (cudaStream_t)g_stream;
+    if (!g_own_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&g_own_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            *rc = cuda_error(e, "cudaStreamCreate");
+            return nullptr;
+        }
+    }
+    return g_own_stream;
+}
+
+int validate_alphabet(const char *alphabet, uint8_t amap[256]) {
+    if (!alphabet) return set_error(MSA_EINVAL, "alphabet is NULL");
+    const size_t A = strlen(alphabet);
+    if (A < 1 || A > MSA_MAX_ALPHABET)
+        return set_error(MSA_EINVAL, "alphabet size %zu outside [1,%d]", A, MSA_MAX_ALPHABET);
+    memset(amap, 0xFF, 256);
+    for (size_t i = 0; i < A; ++i) {
+        const uint8_t c = (uint8_t)alphabet[i];
+        if (amap[c] != 0xFF) return set_error(MSA_EINVAL, "alphabet repeats character '%c'", c);
+        amap[c] = (uint8_t)i;
+    }
+    return MSA_OK;
+}
+
+int validate_request(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
+                     const int32_t *subst, uint8_t amap[256]) {
+    if (k < 2 || k > MSA_MAX_K) return set_error(MSA_EINVAL, "k=%d outside [2,%d]", k, MSA_MAX_K);
+    if (!seqs || !lens || !subst) return set_error(MSA_EINVAL, "NULL seqs, lens or subst");
+    int rc = validate_alphabet(alphabet, amap);
+    if (rc) return rc;
+    const int A = (int)strlen(alphabet);
+    for (int i = 0; i < k; ++i) {
+        if (lens[i] < 0) return set_error(MSA_EINVAL, "lens[%d]=%d is negative", i, lens[i]);
+        if (lens[i] > 0 && !seqs[i]) return set_error(MSA_EINVAL, "seqs[%d] is NULL", i);
+        for (int32_t t = 0; t < lens[i]; ++t)
+            if (amap[(uint8_t)seqs[i][t]] == 0xFF)
+                return set_error(MSA_EINVAL, "sequence %d position %d: residue '%c' not in alphabet", i,
+                                 t, seqs[i][t]);
+    }
+    for (int a = 0; a < A; ++a)
+        for (int b = a + 1; b < A; ++b)
+            if (subst[a * A + b] != subst[b * A + a])
+                return set_error(MSA_EINVAL, "substitution table not symmetric at (%d,%d)", a, b);
+    return MSA_OK;
+}
+
+int status_error(int status) {
+    switch (status) {
+        case MSA_OK: return MSA_OK;
+        case MSA_EINVAL: return set_error(MSA_EINVAL, "device check: residue outside the alphabet or non-symmetric table");
+        case MSA_ETOOBIG: return set_error(MSA_ETOOBIG, "scores could leave the exact int32 range for this table and gap");
+        case MSA_ETIMEOUT: return set_error(MSA_ETIMEOUT, "a device dependency wait exceeded its limit; the fill stopped");
+        default: return set_error(MSA_ECUDA, "device traceback found an inconsistent traceback tensor (status %d)", status);
+    }
+}
+
+int device_sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+int persistent_grid(int k, int kernel, int64_t units) {
+    static int cache[3][MSA_MAX_K + 1] = {};
+    int &c = cache[kernel][k];
+    if (!c) {
+        c = kernel == kKernelCol3 ? fill_col3_ctas_per_sm() : fill_tiles_ctas_per_sm(k);
+        if (c <= 0) c = 1;
+    }
+    const int warps = kernel == kKernelCol3 ? col3_warps_per_cta() : tiles_warps_per_cta(k);
+    int64_t need = (units + warps - 1) / warps;
+    int64_t g = (int64_t)c * device_sm_count();
+    if (need < g) g = need;
+    return (int)(g < 1 ? 1 : g);
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Carve one workspace allocation; `base` may be nullptr to measure only.
+size_t plan_layout(const HostPlan &hp, char *base, PlanPointers *pp, size_t *reset_bytes) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return base ? base + o : nullptr;
+    };
+    char *hdr = take(sizeof(LaunchState));
+    const int64_t nflags = hp.kernel == kKernelCol3 ? hp.ntiles : hp.ntiles;
+    char *done = take((size_t)nflags * 4);
+    *reset_bytes = off;
+    char *order = take((size_t)hp.ntiles * 8);
+    char *prob = take(sizeof(ProblemDesc));
+    char *amap = take(256);
+    char *codes = take((size_t)hp.len_sum + 16);
+    char *tab = take((size_t)hp.A * hp.A * 4);
+    char *qc = take(16);
+    char *tb = take((size_t)hp.tbbytes + 16);
+    char *Q = take((size_t)hp.qelems * 4 + 16);
+    char *aux = take((size_t)hp.aux_elems * 4 + 16);
+    if (pp && base) {
+        LaunchState *ls = reinterpret_cast<LaunchState *>(hdr);
+        pp->state = ls;
+        pp->done = reinterpret_cast<int32_t *>(done);
+        pp->order = reinterpret_cast<uint64_t *>(order);
+        pp->prob = reinterpret_cast<ProblemDesc *>(prob);
+        pp->amap = reinterpret_cast<uint8_t *>(amap);
+        pp->codes = reinterpret_cast<uint8_t *>(codes);
+        pp->tab = reinterpret_cast<int32_t *>(tab);
+        pp->qcorner = reinterpret_cast<int32_t *>(qc);
+        pp->tb = reinterpret_cast<uint8_t *>(tb);
+        pp->Q = reinterpret_cast<int32_t *>(Q);
+        pp->aux = reinterpret_cast<int32_t *>(aux);
+    }
+    return off;
+}
+
+void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_base, ProblemDesc &d) {
+    memset(&d, 0, sizeof d);
+    d.k = hp.k;
+    d.A = hp.A;
+    d.B = hp.k;
+    d.ncode = hp.len_sum;
+    int32_t off = 0;
+    for (int i = 0; i < hp.k; ++i) {
+        d.rho[i] = hp.rho[i];
+        d.len[i] = hp.lens[i];
+        d.cofs[i] = off;
+        off += hp.lens[i];
+        d.G[i] = hp.G[i];
+        d.E[i] = hp.E[i];
+        d.gstride[i] = hp.gstride[i];
+        d.qstride[i] = hp.qstride[i];
+        d.tbstride[i] = hp.tbstride[i];
+    }
+    d.tile_base = tile_base;
+    d.ntiles = hp.ntiles;
+    d.pair_min_sum = hp.pair_min_sum;
+    d.w_corner = hp.w_corner;
+    d.len_sum = hp.len_sum;
+    d.amap = pp.amap;
+    d.codes = pp.codes;
+    d.tab = pp.tab;
+    d.Q = pp.Q;
+    d.aux = pp.aux;
+    d.tb = pp.tb;
+    d.qcorner = pp.qcorner;
+    d.istat = &pp.state->istat;
+}
+
+int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t s) {
+    cudaError_t e = hp.kernel == kKernelCol3 ? launch_fill_col3(L, grid, s)
+                                             : launch_fill_tiles(hp.k, L, grid, s);
+    return e == cudaSuccess ? MSA_OK : cuda_error(e, "fill kernel launch");
+}
+
+}  // namespace msadp
+
+struct msa_plan {
+    HostPlan hp;
+    char alphabet[MSA_MAX_ALPHABET + 1];
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    size_t reset_bytes = 0;
+    PlanPointers pp;
+    int grid = 1;
+    cudaStream_t last_stream = nullptr;
+    // per-stage events of timed executions, a ring of kTimedRing executions
+    static constexpr int kTimedRing = 256;
+    std::vector<cudaEvent_t> ev;
+    int timed = 0;  // executions recorded since the last msa_plan_timings
+};
+
+extern "C" {
+
+const char *msa_last_error(void) { return t_err.c_str(); }
+
+const char *msa_version(void) { return "libmsadp 0.1 (sm_103a)"; }
+
+int msa_set_stream(void *stream) {
+    std::lock_guard<std::mutex> g(settings_mutex());
+    g_stream = stream;
+    g_stream_set = true;
+    return MSA_OK;
+}
+
+int msa_config(const char *key, int64_t value) {
+    if (!key) return set_error(MSA_EINVAL, "NULL key");
+    std::lock_guard<std::mutex> g(settings_mutex());
+    Settings &s = settings();
+    if (!strcmp(key, "spin_timeout_ms")) {
+        if (value < 1) return set_error(MSA_EINVAL, "spin_timeout_ms must be >= 1");
+        s.spin_ms = value;
+    } else if (!strcmp(key, "device_budget_mb")) {
+        if (value < 1) return set_error(MSA_EINVAL, "device_budget_mb must be >= 1");
+        s.budget_mb = value;
+    } else if (!strcmp(key, "max_batch")) {
+        if (value < 1 || value > 4096) return set_error(MSA_EINVAL, "max_batch must be in [1,4096]");
+        s.max_batch = value;
+    } else if (!strcmp(key, "use_graphs")) {
+        s.use_graphs = value ? 1 : 0;
+    } else if (!strcmp(key, "batching")) {
+        s.batching = value ? 1 : 0;
+    } else if (!strcmp(key, "fill_kernel")) {
+        if (value < 0 || value > 2) return set_error(MSA_EINVAL, "fill_kernel must be 0, 1 or 2");
+        s.fill_kernel = value;
+    } else if (!strcmp(key, "timing")) {
+        s.timing = value ? 1 : 0;
+    } else if (!strcmp(key, "test_withhold_tile")) {
+        s.withhold = value;
+    } else {
+        return set_error(MSA_EINVAL, "unknown setting '%s'", key);
+    }
+    return MSA_OK;
+}
+
+int msa_plan_create(int k, const int32_t *lens, const char *alphabet, msa_plan **out_plan) {
+    if (!out_plan) return set_error(MSA_EINVAL, "out_plan is NULL");
+    *out_plan = nullptr;
+    uint8_t amap[256];
+    int rc = validate_alphabet(alphabet, amap);
+    if (rc) return rc;
+    const int A = (int)strlen(alphabet);
+    int kernel_choice;
+    {
+        std::lock_guard<std::mutex> g(settings_mutex());
+        kernel_choice = (int)settings().fill_kernel;
+    }
+    msa_plan *p = new (std::nothrow) msa_plan();
+    if (!p) return set_error(MSA_ENOMEM, "host allocation failed");
+    std::string err;
+    rc = make_plan(k, lens, A, kernel_choice, p->hp, err);
+    if (rc) {
+        delete p;
+        return set_error(rc, "%s", err.c_str());
+    }
+    strncpy(p->alphabet, alphabet, MSA_MAX_ALPHABET);
+    p->ws_bytes = plan_layout(p->hp, nullptr, nullptr, &p->reset_bytes);
+    cudaError_t e = cudaMalloc(&p->ws, p->ws_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        const size_t bytes = p->ws_bytes;
+        delete p;
+        return set_error(e == cudaErrorMemoryAllocation ? MSA_ENOMEM : MSA_ECUDA,
+                         "cudaMalloc of %zu workspace bytes: %s", bytes, cudaGetErrorString(e));
+    }
+    size_t rb = 0;
+    plan_layout(p->hp, p->ws, &p->pp, &rb);
+    ProblemDesc d;
+    fill_problem_desc(p->hp, p->pp, 0, d);
+    e = cudaMemcpy(p->pp.prob, &d, sizeof d, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->pp.order, p->hp.order.data(), p->hp.order.size() * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->pp.amap, amap, 256, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p->ws);
+        delete p;
+        return cuda_error(e, "plan upload");
+    }
+    p->grid = persistent_grid(k, p->hp.kernel, p->hp.ntiles);
+    *out_plan = p;
+    return MSA_OK;
+}
+
+int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_subst, int32_t gap,
+                     msa_device_result *d_result, uint8_t *d_masks, void *stream) {
+    if (!plan || !d_subst || !d_result || (plan->hp.len_sum > 0 && (!d_residues || !d_masks)))
+        return set_error(MSA_EINVAL, "NULL plan or device pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t spin_ms, withhold, timing;
+    {
+        std::lock_guard<std::mutex> g(settings_mutex());
+        spin_ms = settings().spin_ms;
+        withhold = settings().withhold;
+        timing = settings().timing;
+    }
+    plan->last_stream = s;
+    cudaEvent_t *ev = nullptr;
+    if (timing) {
+        if (plan->ev.empty()) {
+            plan->ev.assign(4 * msa_plan::kTimedRing, nullptr);
+            for (auto &x : plan->ev)
+                if (cudaEventCreate(&x) != cudaSuccess) return cuda_error(cudaGetLastError(), "cudaEventCreate");
+        }
+        ev = &plan->ev[4 * (plan->timed % msa_plan::kTimedRing)];
+        cudaEventRecord(ev[0], s);
+    }
+    cudaError_t e = cudaMemsetAsync(plan->ws, 0, plan->reset_bytes, s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+    IODesc io{d_residues, d_subst, d_result, d_masks, gap, 0};
+    e = launch_encode(plan->pp.prob, 1, plan->hp.len_sum, nullptr, io, s);
+    if (e != cudaSuccess) return cuda_error(e, "encode launch");
+    LaunchDesc L;
+    memset(&L, 0, sizeof L);
+    L.probs = plan->pp.prob;
+    L.order = plan->pp.order;
+    L.ntickets = plan->hp.ntiles;
+    L.done = plan->pp.done;
+    L.ticket = &plan->pp.state->ticket;
+    L.err = &plan->pp.state->err;
+    L.spin_ns = spin_ms * 1000000LL;
+    L.withhold = withhold;
+    L.nprob = 1;
+    if (ev) cudaEventRecord(ev[1], s);
+    int rc = launch_fill(plan->hp, L, plan->grid, s);
+    if (rc) return rc;
+    if (ev) cudaEventRecord(ev[2], s);
+    e = launch_traceback(plan->pp.prob, 1, L.err, nullptr, io, s);
+    if (e != cudaSuccess) return cuda_error(e, "traceback launch");
+    if (ev) {
+        cudaEventRecord(ev[3], s);
+        plan->timed++;
+    }
+    return MSA_OK;
+}
+
+int msa_plan_timings(msa_plan *plan, float out_ms[3]) {
+    if (!plan || !out_ms) return set_error(MSA_EINVAL, "NULL plan or output");
+    if (!plan->timed) return set_error(MSA_EINVAL, "no timed execution (enable msa_config(\"timing\", 1))");
+    const int n = plan->timed < msa_plan::kTimedRing ? plan->timed : msa_plan::kTimedRing;
+    const int first = plan->timed - n;
+    double acc[3] = {0, 0, 0};
+    cudaError_t e = cudaSuccess;
+    for (int r = first; r < plan->timed && e == cudaSuccess; ++r) {
+        cudaEvent_t *ev = &plan->ev[4 * (r % msa_plan::kTimedRing)];
+        e = cudaEventSynchronize(ev[3]);
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+            float ms = 0;
+            e = cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            acc[i] += ms;
+        }
+    }
+    plan->timed = 0;
+    if (e != cudaSuccess) return cuda_error(e, "event timing");
+    for (int i = 0; i < 3; ++i) out_ms[i] = (float)(acc[i] / n);
+    return MSA_OK;
+}
+
+int msa_plan_read_tb(msa_plan *plan, void *host_dst, int64_t bytes) {
+    if (!plan || !host_dst || bytes < 0 || bytes > plan->hp.tbbytes)
+        return set_error(MSA_EINVAL, "bad plan, destination or size");
+    cudaError_t e = cudaStreamSynchronize(plan->last_stream);
+    if (e == cudaSuccess) e = cudaMemcpy(host_dst, plan->pp.tb, (size_t)bytes, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? MSA_OK : cuda_error(e, "traceback tensor copy");
+}
+
+int msa_plan_get_info(const msa_plan *plan, msa_plan_info *out) {
+    if (!plan || !out) return set_error(MSA_EINVAL, "NULL plan or info");
+    memset(out, 0, sizeof *out);
+    const HostPlan &hp = plan->hp;
+    out->k = hp.k;
+    out->alphabet_size = hp.A;
+    out->cells = hp.cells;
+    for (int i = 0; i < hp.k; ++i) {
+        out->tb_strides[i] = hp.tbstride[i];
+        out->tile_grid[i] = hp.G[i];
+        out->tile_extent[i] = hp.E[i];
+    }
+    out->tb_bytes = hp.tbbytes;
+    out->workspace_bytes = (int64_t)plan->ws_bytes;
+    out->tiles = hp.ntiles;
+    out->waves = hp.waves;
+    out->fill_kernel = hp.kernel;
+    out->d_tb = plan->pp.tb;
+    return MSA_OK;
+}
+
+int msa_plan_destroy(msa_plan *plan) {
+    if (!plan) return MSA_OK;
+    for (auto &x : plan->ev)
+        if (x) cudaEventDestroy(x);
+    if (plan->ws) cudaFree(plan->ws);
+    delete plan;
+    return MSA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// msa_align: host buffers in, host buffers out, synchronous.
+
+namespace {
+std::mutex g_align_mu;
+msa_plan *g_cached = nullptr;
+char *g_dev_io = nullptr;
+size_t g_dev_io_bytes = 0;
+char *g_host_io = nullptr;
+size_t g_host_io_bytes = 0;
+
+bool same_shape(const msa_plan *p, int k, const int32_t *lens, const char *alphabet, int kernel) {
+    if (!p || p->hp.k != k || strcmp(p->alphabet, alphabet) != 0) return false;
+    if (kernel != kKernelAuto && p->hp.kernel != choose_kernel(k, lens, kernel)) return false;
+    for (int i = 0; i < k; ++i)
+        if (p->hp.lens[i] != lens[i]) return false;
+    return true;
+}
+}  // namespace
+
+int msa_align(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
+              const int32_t *subst, int32_t gap, int32_t *out_score, char *out_alignment) {
+    uint8_t amap[256];
+    int rc = validate_request(k, seqs, lens, alphabet, subst, amap);
+    if (rc) return rc;
+    if (!out_score || !out_alignment) return set_error(MSA_EINVAL, "NULL output pointer");
+    std::lock_guard<std::mutex> g(g_align_mu);
+    int kernel;
+    {
+        std::lock_guard<std::mutex> g2(settings_mutex());
+        kernel = (int)settings().fill_kernel;
+    }
+    if (!same_shape(g_cached, k, lens, alphabet, kernel)) {
+        msa_plan_destroy(g_cached);
+        g_cached = nullptr;
+        rc = msa_plan_create(k, lens, alphabet, &g_cached);
+        if (rc) return rc;
+    }
+    msa_plan *p = g_cached;
+    const int A = p->hp.A;
+    const size_t nres = (size_t)p->hp.len_sum;
+    const size_t off_sub = (nres + 15) & ~(size_t)15;
+    const size_t off_res = (off_sub + (size_t)A * A * 4 + 15) & ~(size_t)15;
+    const size_t off_masks = off_res + 16;
+    const size_t need = off_masks + nres + 16;
+    if (need > g_dev_io_bytes) {
+        if (g_dev_io) cudaFree(g_dev_io);
+        if (g_host_io) cudaFreeHost(g_host_io);
+        g_dev_io = nullptr;
+        g_host_io = nullptr;
+        g_dev_io_bytes = g_host_io_bytes = 0;
+        cudaError_t e = cudaMalloc(&g_dev_io, need * 2);
+        if (e == cudaSuccess) e = cudaMallocHost(&g_host_io, need * 2);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(MSA_ENOMEM, "staging allocation: %s", cudaGetErrorString(e));
+        }
+        g_dev_io_bytes = g_host_io_bytes = need * 2;
+    }
+    cudaStream_t s = library_stream(&rc);
+    if (rc) return rc;
+    // gather inputs into pinned staging, one H2D copy
+    size_t o = 0;
+    for (int i = 0; i < k; ++i) {
+        if (lens[i]) memcpy(g_host_io + o, seqs[i], (size_t)lens[i]);
+        o += (size_t)lens[i];
+    }
+    memcpy(g_host_io + off_sub, subst, (size_t)A * A * 4);
+    cudaError_t e = cudaMemcpyAsync(g_dev_io, g_host_io, off_res, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_error(e, "H2D copy");
+    msa_device_result *d_res = reinterpret_cast<msa_device_result *>(g_dev_io + off_res);
+    uint8_t *d_masks = reinterpret_cast<uint8_t *>(g_dev_io + off_masks);
+    rc = msa_plan_execute(p, g_dev_io, reinterpret_cast<const int32_t *>(g_dev_io + off_sub), gap, d_res,
+                          d_masks, s);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(g_host_io + off_res, g_dev_io + off_res, 16 + nres, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_error(e, "D2H copy");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+    msa_device_result res;
+    memcpy(&res, g_host_io + off_res, sizeof res);
+    rc = status_error(res.status);
+    if (rc) return rc;
+    expand_alignment(k, seqs, lens, reinterpret_cast<const uint8_t *>(g_host_io + off_masks), res.ncols,
+                     out_alignment);
+    *out_score = res.score;
+    return MSA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host-only planner queries.
+
+int msa_wave_sizes(int k, const int32_t *grid, int64_t *out_sizes, int32_t max_waves, int32_t *out_waves) {
+    if (k < 1 || k > MSA_MAX_K || !grid || !out_waves || (max_waves > 0 && !out_sizes))
+        return set_error(MSA_EINVAL, "bad arguments");
+    for (int i = 0; i < k; ++i)
+        if (grid[i] < 1) return set_error(MSA_EINVAL, "grid[%d] < 1", i);
+    std::vector<int64_t> w;
+    wave_sizes(k, grid, w);
+    *out_waves = (int32_t)w.size();
+    for (int32_t i = 0; i < max_waves && i < (int32_t)w.size(); ++i) out_sizes[i] = w[i];
+    return MSA_OK;
+}
+
+int msa_tile_shape(int k, const int32_t *lens, int32_t *out_extent, int32_t *out_grid) {
+    if (k < 2 || k > MSA_MAX_K || !lens || !out_extent || !out_grid)
+        return set_error(MSA_EINVAL, "bad arguments");
+    int kernel;
+    {
+        std::lock_guard<std::mutex> g(settings_mutex());
+        kernel = (int)settings().fill_kernel;
+    }
+    HostPlan hp;
+    std::string err;
+    int rc = make_plan(k, lens, 1, kernel, hp, err);
+    if (rc) return set_error(rc, "%s", err.c_str());
+    for (int i = 0; i < k; ++i) {
+        out_extent[i] = hp.E[i];
+        out_grid[i] = hp.G[i];
+    }
+    return MSA_OK;
+}
+
+}  // extern "C"
+
+namespace msadp {
+
+void expand_alignment(int k, const char *const *seqs, const int32_t *lens, const uint8_t *masks_rev,
+                      int ncols, char *out) {
+    int64_t stride = 1;
+    for (int i = 0; i < k; ++i) stride += lens[i];
+    int32_t pos[MSA_MAX_K] = {};
+    for (int c = 0; c < ncols; ++c) {
+        const int m = masks_rev[ncols - 1 - c];
+        for (int i = 0; i < k; ++i) out[i * stride + c] = ((m >> i) & 1) ? seqs[i][pos[i]++] : '-';
+    }
+    for (int i = 0; i < k; ++i) out[i * stride + ncols] = '\0';
+}
+
+}  // namespace msadp

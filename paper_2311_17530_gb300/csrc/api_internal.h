@@ -1,0 +1,65 @@
+// Host-side helpers shared by api.cpp and serve.cpp.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+
+#include "plan.h"
+
+namespace msadp {
+
+struct Settings {
+    int64_t spin_ms = 5000;
+    int64_t budget_mb = 16384;
+    int64_t max_batch = 64;
+    int64_t use_graphs = 1;
+    int64_t batching = 1;
+    int64_t fill_kernel = 0;
+    int64_t withhold = -1;
+    int64_t timing = 0;
+};
+
+// Header of a workspace; zeroed before every execution.
+struct LaunchState {
+    int32_t ticket;
+    int32_t err;
+    int32_t pad[2];
+    msa_device_result istat;
+};
+
+struct PlanPointers {
+    LaunchState *state = nullptr;
+    int32_t *done = nullptr;
+    uint64_t *order = nullptr;
+    ProblemDesc *prob = nullptr;
+    uint8_t *amap = nullptr;
+    uint8_t *codes = nullptr;
+    int32_t *tab = nullptr;
+    int32_t *qcorner = nullptr;
+    uint8_t *tb = nullptr;
+    int32_t *Q = nullptr;
+    int32_t *aux = nullptr;
+};
+
+constexpr int tiles_warps_per_cta(int k) { return k <= 5 ? 8 : 4; }
+int col3_warps_per_cta();
+
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+Settings &settings();
+std::mutex &settings_mutex();
+cudaStream_t library_stream(int *rc);
+int validate_alphabet(const char *alphabet, uint8_t amap[256]);
+int validate_request(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
+                     const int32_t *subst, uint8_t amap[256]);
+int status_error(int status);
+int persistent_grid(int k, int kernel, int64_t units);
+size_t plan_layout(const HostPlan &hp, char *base, PlanPointers *pp, size_t *reset_bytes);
+void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_base, ProblemDesc &d);
+int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t s);
+void expand_alignment(int k, const char *const *seqs, const int32_t *lens, const uint8_t *masks_rev,
+                      int ncols, char *out);
+
+}  // namespace msadp

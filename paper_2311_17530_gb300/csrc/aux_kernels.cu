@@ -1,0 +1,187 @@
+// Encode + table kernel (hot-path step a1) and the single-warp traceback kernel
+// (step a4), plus the per-k dispatch of the generic tile fill.
+#include "device_common.cuh"
+
+namespace msadp {
+
+// Residues -> alphabet codes; pair table scaled for the packed-key fill:
+// tab[a][b] = (sub[a][b] - 2 gap) << k. Rejects residues outside the alphabet
+// and non-symmetric tables (MSA_EINVAL), and any table whose keys could leave
+// the exact int32 range (MSA_ETOOBIG), by writing the problem's status word.
+__global__ void encode_kernel(const ProblemDesc *probs, const IODesc *io_arr, IODesc io1) {
+    const int p = blockIdx.y;
+    const ProblemDesc &P = probs[p];
+    const IODesc io = io_arr ? io_arr[p] : io1;
+    msa_device_result *st = P.istat;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.ncode; i += gridDim.x * blockDim.x) {
+        const uint8_t c = P.amap[(uint8_t)io.residues[i]];
+        if (c == 0xFF) atomicCAS(&st->status, 0, MSA_EINVAL);
+        P.codes[i] = (c == 0xFF) ? (uint8_t)0 : c;
+    }
+    if (blockIdx.x != 0) return;
+    __shared__ int smax, sbad;
+    if (threadIdx.x == 0) {
+        smax = 0;
+        sbad = 0;
+    }
+    __syncthreads();
+    const int A = P.A, B = P.B;
+    int lmax = 0, lbad = 0;
+    for (int i = threadIdx.x; i < A * A; i += blockDim.x) {
+        const int a = i / A, b = i - a * A;
+        const int64_t v = io.subst[i];
+        if (v != (int64_t)io.subst[b * A + a]) lbad = 1;
+        const int64_t pp = v - 2 * (int64_t)io.gap;
+        const int64_t ap = pp < 0 ? -pp : pp;
+        if (ap > (1 << 20)) {
+            lmax = 1 << 21;
+            P.tab[i] = 0;
+        } else {
+            lmax = max(lmax, (int)ap);
+            P.tab[i] = (int32_t)(pp * (1 << B));
+        }
+    }
+    atomicMax(&smax, lmax);
+    if (lbad) atomicOr(&sbad, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (sbad) atomicCAS(&st->status, 0, MSA_EINVAL);
+        const int64_t npairs = (int64_t)P.k * (P.k - 1) / 2;
+        const int64_t key_bound =
+            (int64_t)smax * (P.pair_min_sum + npairs) * ((int64_t)1 << B) + P.w_corner;
+        const int64_t g = io.gap < 0 ? -(int64_t)io.gap : (int64_t)io.gap;
+        const int64_t score_bound = (int64_t)smax * P.pair_min_sum + g * (P.k - 1) * P.len_sum;
+        if (key_bound >= kKeyLimit || score_bound >= ((int64_t)1 << 31) - 1)
+            atomicCAS(&st->status, 0, MSA_ETOOBIG);
+    }
+}
+
+cudaError_t launch_encode(const ProblemDesc *d_probs, int nprob, int max_ncode,
+                          const IODesc *io_array, IODesc io_single, cudaStream_t s) {
+    int bx = (max_ncode + 255) / 256;
+    if (bx < 1) bx = 1;
+    if (bx > 64) bx = 64;
+    encode_kernel<<<dim3(bx, nprob), 256, 0, s>>>(d_probs, io_array, io_single);
+    return cudaGetLastError();
+}
+
+// Traceback (section 2): from the far corner follow the stored move of every
+// cell back to the origin. One warp per problem: the warp stages the box
+// [x - D, x] of the traceback tensor into shared memory with coalesced 4-byte
+// loads, lane 0 walks the path inside the box until it leaves through a lower
+// face, and the next box is staged around the new position. The masks are
+// written last column first; the score is decoded from the corner's packed key.
+__global__ void __launch_bounds__(32) traceback_kernel(const ProblemDesc *probs, const int32_t *err,
+                                                       const IODesc *io_arr, IODesc io1) {
+    const int p = blockIdx.x;
+    const ProblemDesc &P = probs[p];
+    const IODesc io = io_arr ? io_arr[p] : io1;
+    extern __shared__ __align__(16) unsigned char box[];
+    const int lane = threadIdx.x;
+    int status = ld_volatile(&P.istat->status);
+    if (status == 0 && err) status = ld_volatile(err);
+    if (status != 0) {
+        if (lane == 0) {
+            io.result->status = status;
+            io.result->score = 0;
+            io.result->ncols = 0;
+        }
+        return;
+    }
+    const int K = P.k, B = P.B;
+    const int D = traceback_box(K);
+    int x[MSA_MAX_K], lo[MSA_MAX_K], ext[MSA_MAX_K];
+    int64_t bs[MSA_MAX_K];
+    for (int i = 0; i < K; ++i) x[i] = P.len[i];
+    int ncols = 0;
+    int fail = 0;
+    while (true) {
+        bool any = false;
+        for (int i = 0; i < K; ++i) any = any || x[i] > 0;
+        if (!any || fail) break;
+        for (int i = 0; i < K; ++i) lo[i] = max(0, x[i] - D);
+        const int a = lo[K - 1] & ~3;
+        const int rowb = round_up(x[K - 1] - a + 1, 4);
+        bs[K - 1] = 1;
+        int64_t stride = rowb;
+        for (int i = K - 2; i >= 0; --i) {
+            bs[i] = stride;
+            ext[i] = x[i] - lo[i] + 1;
+            stride *= ext[i];
+        }
+        const int wpr = rowb / 4;
+        const int words = (int)(stride / 4);
+        for (int w = lane; w < words; w += 32) {
+            const int row = w / wpr, cw = w - row * wpr;
+            int r = row;
+            int64_t g = a + 4 * cw;
+            for (int i = K - 2; i >= 0; --i) {
+                const int ci = r % ext[i];
+                r /= ext[i];
+                g += (int64_t)(lo[i] + ci) * P.tbstride[i];
+            }
+            const uint32_t v = __ldcg(reinterpret_cast<const unsigned int *>(P.tb + g));
+            *reinterpret_cast<uint32_t *>(box + (int64_t)row * rowb + 4 * cw) = v;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            int64_t li = x[K - 1] - a;
+            for (int i = 0; i < K - 1; ++i) li += (int64_t)(x[i] - lo[i]) * bs[i];
+            while (true) {
+                bool any2 = false;
+                for (int i = 0; i < K; ++i) any2 = any2 || x[i] > 0;
+                if (!any2) break;
+                const int m = box[li];
+                bool bad = (m == 0) || (m >> K) != 0 || ncols >= P.len_sum;
+                for (int i = 0; i < K; ++i)
+                    if (((m >> i) & 1) && x[i] == 0) bad = true;
+                if (bad) {
+                    fail = 1;
+                    break;
+                }
+                io.masks[ncols++] = (uint8_t)m;
+                bool out = false;
+                for (int i = 0; i < K; ++i)
+                    if ((m >> i) & 1) {
+                        x[i] -= 1;
+                        li -= bs[i];
+                        if (x[i] < lo[i]) out = true;
+                    }
+                if (out) break;
+            }
+        }
+        for (int i = 0; i < K; ++i) x[i] = __shfl_sync(kFull, x[i], 0);
+        ncols = __shfl_sync(kFull, ncols, 0);
+        fail = __shfl_sync(kFull, fail, 0);
+        __syncwarp();
+    }
+    if (lane == 0) {
+        const int q = *P.qcorner;
+        const int hprime = (q - P.w_corner) >> B;  // exact: q = H' * 2^B + W(corner)
+        io.result->score = hprime + io.gap * (K - 1) * P.len_sum;
+        io.result->ncols = ncols;
+        io.result->status = fail ? MSA_ECUDA : MSA_OK;
+    }
+}
+
+cudaError_t launch_traceback(const ProblemDesc *d_probs, int nprob, const int32_t *err,
+                             const IODesc *io_array, IODesc io_single, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(traceback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kTracebackSmem);
+    if (e != cudaSuccess) return e;
+    traceback_kernel<<<nprob, 32, kTracebackSmem, s>>>(d_probs, err, io_array, io_single);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_tiles_lo(int k, const LaunchDesc &L, int grid, cudaStream_t s);
+cudaError_t launch_fill_tiles_hi(int k, const LaunchDesc &L, int grid, cudaStream_t s);
+int fill_tiles_ctas_lo(int k);
+int fill_tiles_ctas_hi(int k);
+
+cudaError_t launch_fill_tiles(int k, const LaunchDesc &L, int grid, cudaStream_t s) {
+    return k <= 4 ? launch_fill_tiles_lo(k, L, grid, s) : launch_fill_tiles_hi(k, L, grid, s);
+}
+
+int fill_tiles_ctas_per_sm(int k) { return k <= 4 ? fill_tiles_ctas_lo(k) : fill_tiles_ctas_hi(k); }
+
+}  // namespace msadp

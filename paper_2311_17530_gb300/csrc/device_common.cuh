@@ -1,0 +1,118 @@
+// Device helpers shared by the fill and traceback kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace msadp {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ int ld_acquire(const int32_t *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int32_t *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_volatile(const int32_t *p) {
+    return *reinterpret_cast<const volatile int32_t *>(p);
+}
+
+// Bounded wait until *flag >= need. Returns false when the launch status is set
+// by another warp or when the wait exceeds spin_ns (then the caller records
+// MSA_ETIMEOUT and leaves). Never traps; every exit path is finite.
+__device__ __forceinline__ bool wait_at_least(const int32_t *flag, int need, const int32_t *err,
+                                              int64_t spin_ns) {
+    if (ld_acquire(flag) >= need) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1; it < (1u << 27); ++it) {
+        if (ld_acquire(flag) >= need) return true;
+        if ((it & 31) == 0) {
+            if (ld_volatile(err) != 0) return false;
+            if ((int64_t)(global_ns() - t0) > spin_ns) return false;
+        }
+        __nanosleep(it < 64 ? 32 : 256);
+    }
+    return false;
+}
+
+// Geometry of the generic tile kernel (compile-time per k).
+__host__ __device__ constexpr int geo_sh(int K, int i) {  // halo'd tile stride
+    int s = 1;
+    for (int j = K - 1; j > i; --j) s *= tile_extent(K, j) + 1;
+    return s;
+}
+__host__ __device__ constexpr int geo_st(int K, int i) {  // interior tile stride
+    int s = 1;
+    for (int j = K - 1; j > i; --j) s *= tile_extent(K, j);
+    return s;
+}
+__host__ __device__ constexpr int geo_volh(int K) { return geo_sh(K, -1); }
+__host__ __device__ constexpr int geo_vol(int K) { return geo_st(K, -1); }
+__host__ __device__ constexpr int geo_planes(int K) {
+    int s = 0;
+    for (int i = 0; i < K; ++i) s += tile_extent(K, i);
+    return s - K + 1;
+}
+__host__ __device__ constexpr int geo_codes(int K) {
+    int s = 0;
+    for (int i = 0; i < K; ++i) s += tile_extent(K, i);
+    return s;
+}
+__host__ __device__ constexpr int geo_code_base(int K, int i) {
+    int s = 0;
+    for (int j = 0; j < i; ++j) s += tile_extent(K, j);
+    return s;
+}
+// smem offset of the predecessor x - e_m relative to x
+__host__ __device__ constexpr int move_soff(int K, int m) {
+    int s = 0;
+    for (int i = 0; i < K; ++i)
+        if ((m >> i) & 1) s += geo_sh(K, i);
+    return s;
+}
+// cells of halo face f: first axis at local -1 is f
+__host__ __device__ constexpr int face_extent(int K, int f, int j) {
+    return j < f ? tile_extent(K, j) : (j == f ? 1 : tile_extent(K, j) + 1);
+}
+__host__ __device__ constexpr int face_size(int K, int f) {
+    int s = 1;
+    for (int j = 0; j < K; ++j) s *= face_extent(K, f, j);
+    return s;
+}
+__host__ __device__ constexpr int face_stride(int K, int f, int i) {
+    int s = 1;
+    for (int j = K - 1; j > i; --j) s *= face_extent(K, f, j);
+    return s;
+}
+__host__ __device__ constexpr int popc_c(int m) {
+    int c = 0;
+    while (m) {
+        c += m & 1;
+        m >>= 1;
+    }
+    return c;
+}
+__host__ __device__ constexpr int highbit_c(int m) {
+    int h = -1;
+    while (m) {
+        m >>= 1;
+        ++h;
+    }
+    return h;
+}
+__host__ __device__ constexpr int round_up(int x, int a) { return (x + a - 1) / a * a; }
+
+}  // namespace msadp

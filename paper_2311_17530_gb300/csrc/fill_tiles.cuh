@@ -1,0 +1,307 @@
+// Generic persistent hyper-tile fill for any k in [2, 8].
+//
+// The k-dimensional tensor (section 2) is cut into hyper-tiles of compile-time
+// extents E_i (the paper's partitions of size S, section 3, but without overlap:
+// a tile reads a one-cell halo from its lower neighbours instead). Tiles are
+// handed out by an atomic ticket in wave order (tiles of equal index sum,
+// section 3: "partitions at equal distance from the origin"); a tile starts once
+// its k face predecessors have published completion (bounded acquire waits),
+// which also covers every edge and corner predecessor transitively.
+//
+// One warp fills one tile in shared memory: the halo comes from the score
+// scratch in global memory (L2, bypassing L1), then the warp sweeps the tile's
+// own intra-tile hyperplanes (cells of equal local index sum are independent),
+// one cell per lane, each cell taking the max over its 2^k - 1 predecessors with
+// the packed-key add-max (DPX viaddmax). Finally the tile's scores and traceback
+// bytes are written back and the tile's flag is released.
+#pragma once
+
+#include "device_common.cuh"
+
+namespace msadp {
+
+template <int K>
+struct TilesCfg {
+    static constexpr int WARPS = K <= 5 ? 8 : 4;
+};
+
+template <int K>
+__host__ __device__ constexpr int tiles_warp_bytes() {
+    return round_up(geo_volh(K) * 4, 16) + round_up(geo_vol(K), 16) + round_up(geo_codes(K), 16);
+}
+
+template <int K>
+__host__ __device__ constexpr int tiles_smem_bytes() {
+    return round_up(geo_vol(K) * 8, 16) + round_up(geo_planes(K) + 1, 4) * 4 +
+           round_up(geo_planes(K), 4) * 4 + TilesCfg<K>::WARPS * tiles_warp_bytes<K>();
+}
+
+template <int K>
+__global__ void __launch_bounds__(TilesCfg<K>::WARPS * 32)
+fill_tiles_kernel(const LaunchDesc L) {
+    constexpr int VOL = geo_vol(K);
+    constexpr int VOLH = geo_volh(K);
+    constexpr int PLANES = geo_planes(K);
+    constexpr int NM = (1 << K) - 1;
+    constexpr int CB = K <= 4 ? 8 : 4;  // bits per packed local coordinate
+    constexpr unsigned CMASK = (1u << CB) - 1;
+    constexpr int MASKB = (1 << K) - 1;  // tie bits B = k
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint2 *sched = reinterpret_cast<uint2 *>(smem);
+    int *pstart = reinterpret_cast<int *>(smem + round_up(VOL * 8, 16));
+    int *pcur = pstart + round_up(PLANES + 1, 4);
+    unsigned char *wbase = reinterpret_cast<unsigned char *>(pcur + round_up(PLANES, 4));
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    // Intra-tile schedule: every cell of a full tile, grouped by local index sum.
+    for (int s = tid; s < PLANES; s += blockDim.x) pcur[s] = 0;
+    __syncthreads();
+    for (int i = tid; i < VOL; i += blockDim.x) {
+        int s = 0, rem = i;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int c = rem / geo_st(K, j);
+            rem -= c * geo_st(K, j);
+            s += c;
+        }
+        atomicAdd(&pcur[s], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int s = 0; s < PLANES; ++s) {
+            pstart[s] = acc;
+            acc += pcur[s];
+            pcur[s] = pstart[s];
+        }
+        pstart[PLANES] = acc;
+    }
+    __syncthreads();
+    for (int i = tid; i < VOL; i += blockDim.x) {
+        int s = 0, rem = i, soff = 0;
+        uint32_t pk = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int c = rem / geo_st(K, j);
+            rem -= c * geo_st(K, j);
+            s += c;
+            soff += (c + 1) * geo_sh(K, j);
+            pk |= (uint32_t)c << (CB * j);
+        }
+        const int pos = atomicAdd(&pcur[s], 1);
+        sched[pos] = make_uint2((uint32_t)soff | ((uint32_t)i << 16), pk);
+    }
+    __syncthreads();
+
+    int32_t *qs = reinterpret_cast<int32_t *>(wbase + warp * tiles_warp_bytes<K>());
+    unsigned char *tbs = reinterpret_cast<unsigned char *>(qs) + round_up(VOLH * 4, 16);
+    unsigned char *tcs = tbs + round_up(VOL, 16);
+
+    while (true) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(L.ticket, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if ((int64_t)t >= L.ntickets) break;
+        if (ld_volatile(L.err) != 0) break;
+        const uint64_t ent = L.order[t];
+        const ProblemDesc &P = L.probs[(int)(ent >> 32)];
+        const int64_t lin = (int64_t)(uint32_t)ent;
+
+        int o[K], e[K], tco[K], len[K], cofs[K];
+        int64_t qstr[K], tstr[K];
+        int64_t rem = lin;
+        bool corner = true, origin = true;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int64_t gs = P.gstride[j];
+            tco[j] = (int)(rem / gs);
+            rem -= tco[j] * gs;
+            o[j] = tco[j] * tile_extent(K, j);
+            const int rho = P.rho[j];
+            e[j] = min(tile_extent(K, j), rho - o[j]);
+            corner = corner && (o[j] + e[j] == rho);
+            origin = origin && (o[j] == 0);
+            len[j] = P.len[j];
+            cofs[j] = P.cofs[j];
+            qstr[j] = P.qstride[j];
+            tstr[j] = P.tbstride[j];
+        }
+        const int64_t tile_base = P.tile_base;
+
+        // Wait for the face predecessors (one lane per axis).
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (lane == j && tco[j] > 0)
+                ok = wait_at_least(&L.done[tile_base + lin - P.gstride[j]], 1, L.err, L.spin_ns);
+        if (!__all_sync(kFull, ok)) {
+            if (lane == 0) atomicCAS(L.err, 0, MSA_ETIMEOUT);
+            break;
+        }
+        __threadfence();
+
+        if (ld_volatile(&P.istat->status) == 0) {
+            const int A = P.A;
+            const int32_t *__restrict__ tab = P.tab;
+            const uint8_t *__restrict__ codes = P.codes;
+            const int32_t *__restrict__ Qg = P.Q;
+
+            // Residue codes entering each local coordinate (x_j = o_j + c consumes
+            // residue x_j - 1 of sequence j).
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+                for (int c = lane; c < tile_extent(K, j); c += 32) {
+                    const int x = o[j] + c;
+                    tcs[geo_code_base(K, j) + c] =
+                        (x >= 1 && x <= len[j]) ? codes[cofs[j] + x - 1] : (uint8_t)0;
+                }
+
+            // Halo: every cell with some local coordinate -1, face by face.
+#pragma unroll
+            for (int f = 0; f < K; ++f) {
+                for (int i = lane; i < face_size(K, f); i += 32) {
+                    int r = i, soff = 0;
+                    bool in = true, neg = false;
+                    int64_t g = 0;
+#pragma unroll
+                    for (int j = 0; j < K; ++j) {
+                        const int fs = face_stride(K, f, j);
+                        int cj = r / fs;
+                        r -= cj * fs;
+                        if (j >= f) cj -= 1;
+                        in = in && (cj < e[j]);
+                        neg = neg || (cj < 0 && o[j] == 0);
+                        soff += (cj + 1) * geo_sh(K, j);
+                        g += (int64_t)(o[j] + cj) * qstr[j];
+                    }
+                    if (in) qs[soff] = neg ? kNeg : __ldcg(Qg + g);
+                }
+            }
+            __syncwarp();
+
+            int Wo = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) Wo += o[j] << j;
+
+            for (int s = 0; s < PLANES; ++s) {
+                const int b = pstart[s], en = pstart[s + 1];
+                for (int idx = b + lane; idx < en; idx += 32) {
+                    const uint2 sc = sched[idx];
+                    const int soff = (int)(sc.x & 0xFFFFu), toff = (int)(sc.x >> 16);
+                    int c[K], wl = 0;
+                    bool in = true;
+#pragma unroll
+                    for (int j = 0; j < K; ++j) {
+                        c[j] = (int)((sc.y >> (CB * j)) & CMASK);
+                        in = in && (c[j] < e[j]);
+                        wl += c[j] << j;
+                    }
+                    if (!in) continue;
+                    if (origin && s == 0) {  // H(0) = 0
+                        qs[soff] = 0;
+                        tbs[toff] = 0;
+                        continue;
+                    }
+                    int a[K];
+#pragma unroll
+                    for (int j = 0; j < K; ++j) a[j] = tcs[geo_code_base(K, j) + c[j]];
+                    int pv[K][K];
+#pragma unroll
+                    for (int i = 0; i < K; ++i)
+#pragma unroll
+                        for (int j = i + 1; j < K; ++j) pv[i][j] = __ldg(tab + a[i] * A + a[j]);
+                    // S[m] = sum of scaled pair scores over pairs inside move m,
+                    // built by highest element: S[r | h] = S[r] + T_h[r],
+                    // T_h[r] = sum_{l in r} pv[l][h].
+                    int S[NM + 1];
+                    S[0] = 0;
+#pragma unroll
+                    for (int h = 0; h < K; ++h) {
+                        int T[1 << (K - 1)];
+                        T[0] = 0;
+#pragma unroll
+                        for (int r2 = 1; r2 < (1 << h); ++r2) {
+                            const int l = highbit_c(r2);
+                            T[r2] = T[r2 ^ (1 << l)] + pv[l][h];
+                        }
+#pragma unroll
+                        for (int r2 = 0; r2 < (1 << h); ++r2) S[r2 | (1 << h)] = S[r2] + T[r2];
+                    }
+                    int acc = kNeg;
+#pragma unroll
+                    for (int m = 1; m <= NM; ++m) {
+                        const int pred = qs[soff - move_soff(K, m)];
+                        if (popc_c(m) == 1)
+                            acc = max(acc, pred);
+                        else
+                            acc = __viaddmax_s32(pred, S[m], acc);
+                    }
+                    const int tmask = (Wo + wl - acc) & MASKB;
+                    qs[soff] = acc + tmask;
+                    tbs[toff] = (unsigned char)tmask;
+                }
+                __syncwarp();
+            }
+
+            // Write back scores (for successor halos) and traceback bytes.
+            int32_t *__restrict__ Qw = P.Q;
+            uint8_t *__restrict__ tbw = P.tb;
+            for (int i = lane; i < VOL; i += 32) {
+                int r = i, soff = 0;
+                bool in = true;
+                int64_t gq = 0, gt = 0;
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const int cj = r / geo_st(K, j);
+                    r -= cj * geo_st(K, j);
+                    in = in && (cj < e[j]);
+                    soff += (cj + 1) * geo_sh(K, j);
+                    gq += (int64_t)(o[j] + cj) * qstr[j];
+                    gt += (int64_t)(o[j] + cj) * tstr[j];
+                }
+                if (in) {
+                    Qw[gq] = qs[soff];
+                    tbw[gt] = tbs[i];
+                }
+            }
+            if (corner && lane == 0) {
+                int soff = 0;
+#pragma unroll
+                for (int j = 0; j < K; ++j) soff += e[j] * geo_sh(K, j);
+                *P.qcorner = qs[soff];
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && (int64_t)t != L.withhold) {
+            __threadfence();
+            st_release(&L.done[tile_base + lin], 1);
+        }
+    }
+}
+
+template <int K>
+cudaError_t launch_tiles_k(const LaunchDesc &L, int grid, cudaStream_t s) {
+    constexpr int smem = tiles_smem_bytes<K>();
+    cudaError_t e = cudaFuncSetAttribute(fill_tiles_kernel<K>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    fill_tiles_kernel<K><<<grid, TilesCfg<K>::WARPS * 32, smem, s>>>(L);
+    return cudaGetLastError();
+}
+
+template <int K>
+int tiles_ctas_k() {
+    constexpr int smem = tiles_smem_bytes<K>();
+    if (cudaFuncSetAttribute(fill_tiles_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fill_tiles_kernel<K>,
+                                                      TilesCfg<K>::WARPS * 32, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+}  // namespace msadp

@@ -1,0 +1,138 @@
+// Host planner (hot-path step a2): shape rho_i = len_i + 1 (section 3.2), the
+// mixed-radix row-major linear index of the tensor (section 2's shape- and
+// dimension-invariant indexing: l = sum_i x_i * stride_i with the last axis
+// fastest), the tile grid, and the ticket order of tiles by wave (section 3:
+// tiles whose coordinates sum to w form wave w and are mutually independent).
+#include "plan.h"
+
+#include <algorithm>
+#include <cstdio>
+
+namespace msadp {
+
+int choose_kernel(int k, const int32_t *lens, int requested) {
+    (void)lens;
+    if (requested == kKernelCol3) return k == 3 ? kKernelCol3 : kKernelTiles;
+    if (requested == kKernelTiles) return kKernelTiles;
+    return kKernelTiles;
+}
+
+void tile_extents(int k, const int32_t *lens, int kernel, int32_t *E) {
+    (void)lens;
+    (void)kernel;
+    for (int i = 0; i < k; ++i) E[i] = tile_extent(k, i);
+}
+
+void wave_sizes(int k, const int32_t *grid, std::vector<int64_t> &out) {
+    // Number of grid points with coordinate sum w: the product of the axes'
+    // generating polynomials (1 + z + ... + z^(G_i - 1)), coefficient by coefficient.
+    std::vector<int64_t> cur(1, 1);
+    for (int i = 0; i < k; ++i) {
+        const int g = std::max(grid[i], 1);
+        std::vector<int64_t> nxt(cur.size() + g - 1, 0);
+        for (size_t w = 0; w < cur.size(); ++w)
+            for (int v = 0; v < g; ++v) nxt[w + v] += cur[w];
+        cur.swap(nxt);
+    }
+    out = cur;
+}
+
+static int64_t round_up64(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err) {
+    char buf[256];
+    if (k < 2 || k > MSA_MAX_K) {
+        snprintf(buf, sizeof buf, "k=%d outside [2,%d]", k, MSA_MAX_K);
+        err = buf;
+        return MSA_EINVAL;
+    }
+    if (!lens) {
+        err = "lens is NULL";
+        return MSA_EINVAL;
+    }
+    if (A < 1 || A > MSA_MAX_ALPHABET) {
+        snprintf(buf, sizeof buf, "alphabet size %d outside [1,%d]", A, MSA_MAX_ALPHABET);
+        err = buf;
+        return MSA_EINVAL;
+    }
+    hp = HostPlan();
+    hp.k = k;
+    hp.A = A;
+    hp.kernel = choose_kernel(k, lens, kernel_choice);
+    long double cells = 1;
+    int64_t len_sum = 0, w_corner = 0, pair_min = 0;
+    for (int i = 0; i < k; ++i) {
+        if (lens[i] < 0) {
+            snprintf(buf, sizeof buf, "lens[%d]=%d is negative", i, lens[i]);
+            err = buf;
+            return MSA_EINVAL;
+        }
+        hp.lens[i] = lens[i];
+        hp.rho[i] = lens[i] + 1;
+        cells *= (long double)hp.rho[i];
+        len_sum += lens[i];
+        w_corner += (int64_t)lens[i] << i;
+        for (int j = i + 1; j < k; ++j) pair_min += std::min(lens[i], lens[j]);
+    }
+    if (cells > (long double)(1LL << 38) || len_sum >= (1 << 24) || w_corner >= (1 << 28)) {
+        snprintf(buf, sizeof buf, "tensor of %.3Lg cells is beyond the supported size", cells);
+        err = buf;
+        return MSA_ETOOBIG;
+    }
+    hp.cells = (int64_t)cells;
+    hp.len_sum = (int32_t)len_sum;
+    hp.w_corner = (int32_t)w_corner;
+    hp.pair_min_sum = (int32_t)std::min<int64_t>(pair_min, (1LL << 30));
+
+    tile_extents(k, lens, hp.kernel, hp.E);
+    int64_t nt = 1;
+    for (int i = k - 1; i >= 0; --i) {
+        hp.G[i] = (hp.rho[i] + hp.E[i] - 1) / hp.E[i];
+        hp.gstride[i] = nt;
+        nt *= hp.G[i];
+    }
+    if (nt >= (1LL << 32)) {
+        err = "too many tiles";
+        return MSA_ETOOBIG;
+    }
+    hp.ntiles = nt;
+    int gsum = 0;
+    for (int i = 0; i < k; ++i) gsum += hp.G[i];
+    hp.waves = gsum - k + 1;
+
+    // score scratch: full tensor, last axis padded to 4 elements (16-byte rows)
+    int64_t s = 1;
+    for (int i = k - 1; i >= 0; --i) {
+        hp.qstride[i] = s;
+        s *= (i == k - 1) ? round_up64(hp.rho[i], 4) : hp.rho[i];
+    }
+    hp.qelems = s;
+    // traceback tensor: row-major, last axis padded to 4 bytes
+    s = 1;
+    for (int i = k - 1; i >= 0; --i) {
+        hp.tbstride[i] = s;
+        s *= (i == k - 1) ? round_up64(hp.rho[i], 4) : hp.rho[i];
+    }
+    hp.tbbytes = s;
+
+    // ticket order: by wave, then by linear tile index (counting sort)
+    std::vector<int64_t> cnt(hp.waves + 1, 0);
+    std::vector<int32_t> wave_of(nt);
+    for (int64_t t = 0; t < nt; ++t) {
+        int64_t rem = t;
+        int w = 0;
+        for (int i = 0; i < k; ++i) {
+            const int64_t c = rem / hp.gstride[i];
+            rem -= c * hp.gstride[i];
+            w += (int)c;
+        }
+        wave_of[t] = w;
+        cnt[w + 1]++;
+    }
+    for (int w = 0; w < hp.waves; ++w) cnt[w + 1] += cnt[w];
+    hp.order.assign(nt, 0);
+    for (int64_t t = 0; t < nt; ++t) hp.order[cnt[wave_of[t]]++] = (uint64_t)t;
+    return MSA_OK;
+}
+
+}  // namespace msadp

@@ -1,0 +1,50 @@
+// Host planner: tensor shape, mixed-radix strides, tile grid and wave order.
+#pragma once
+
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace msadp {
+
+enum FillKernel { kKernelAuto = 0, kKernelTiles = 1, kKernelCol3 = 2 };
+
+struct HostPlan {
+    int k = 0;
+    int A = 0;
+    int kernel = kKernelTiles;
+    int32_t lens[MSA_MAX_K] = {};
+    int32_t rho[MSA_MAX_K] = {};
+    int64_t cells = 0;
+    int32_t E[MSA_MAX_K] = {};     // tile extents
+    int32_t G[MSA_MAX_K] = {};     // tile grid
+    int64_t gstride[MSA_MAX_K] = {};
+    int64_t ntiles = 0;            // work units (tiles, or columns for the k=3 kernel)
+    int32_t waves = 0;
+    int64_t qstride[MSA_MAX_K] = {};
+    int64_t qelems = 0;            // score scratch elements
+    int64_t aux_elems = 0;         // second scratch array (column kernel)
+    int64_t tbstride[MSA_MAX_K] = {};
+    int64_t tbbytes = 0;
+    int32_t pair_min_sum = 0;
+    int32_t w_corner = 0;
+    int32_t len_sum = 0;
+    std::vector<uint64_t> order;   // ticket -> tile linear index (problem bits added by callers)
+};
+
+// Tile (or column) extents the planner uses for these lengths and kernel.
+void tile_extents(int k, const int32_t *lens, int kernel, int32_t *E);
+
+// Fill `hp` for one problem. Returns MSA_OK or an MSA_E* code with `err` set.
+int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err);
+
+// Units on each wave of a grid (tiles whose coordinates sum to w), w = 0, 1, ...
+void wave_sizes(int k, const int32_t *grid, std::vector<int64_t> &out);
+
+// Which fill kernel runs for this shape when the caller leaves the choice open.
+int choose_kernel(int k, const int32_t *lens, int requested);
+
+}  // namespace msadp

@@ -1,0 +1,290 @@
+"""Thin ctypes binding of libmsadp (argument marshalling only).
+
+Every step of the alignment runs inside libmsadp's CUDA kernels; this module only
+converts Python values to the C-ABI declared in include/msadp.h and back. There
+is no fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libmsadp.so")
+
+MSA_OK = 0
+MSA_PENDING = 1
+MSA_EINVAL = -1
+MSA_ETOOBIG = -2
+MSA_ENOMEM = -3
+MSA_ECUDA = -4
+MSA_ETIMEOUT = -5
+MSA_EBADHANDLE = -6
+MAX_K = 8
+
+_NAMES = {MSA_EINVAL: "MSA_EINVAL", MSA_ETOOBIG: "MSA_ETOOBIG", MSA_ENOMEM: "MSA_ENOMEM",
+          MSA_ECUDA: "MSA_ECUDA", MSA_ETIMEOUT: "MSA_ETIMEOUT", MSA_EBADHANDLE: "MSA_EBADHANDLE"}
+
+EXPORTED = ["msa_align", "msa_last_error", "msa_set_stream", "msa_config", "msa_plan_create",
+            "msa_plan_execute", "msa_plan_get_info", "msa_plan_destroy", "msa_submit", "msa_poll",
+            "msa_cancel", "msa_drain", "msa_wave_sizes", "msa_tile_shape", "msa_version",
+            "msa_plan_read_tb", "msa_plan_timings"]
+
+
+class MsaError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {message}")
+        self.code = code
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("alphabet_size", ctypes.c_int32), ("cells", ctypes.c_int64),
+                ("tb_strides", ctypes.c_int64 * MAX_K), ("tb_bytes", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_int64), ("tile_grid", ctypes.c_int32 * MAX_K),
+                ("tile_extent", ctypes.c_int32 * MAX_K), ("tiles", ctypes.c_int64),
+                ("waves", ctypes.c_int32), ("fill_kernel", ctypes.c_int32), ("d_tb", ctypes.c_void_p)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("seqs", ctypes.POINTER(ctypes.c_char_p)),
+                ("lens", ctypes.POINTER(ctypes.c_int32)), ("alphabet", ctypes.c_char_p),
+                ("subst", ctypes.POINTER(ctypes.c_int32)), ("gap", ctypes.c_int32)]
+
+
+DEVICE_RESULT_BYTES = 16  # msa_device_result: score, ncols, status, pad (int32 each)
+
+_lib = None
+
+
+def library() -> ctypes.CDLL:
+    """The loaded libmsadp (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libmsadp is not built ({LIB_PATH} missing); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    L.msa_align.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), i32p, ctypes.c_char_p, i32p,
+                            ctypes.c_int32, i32p, ctypes.c_char_p]
+    L.msa_last_error.restype = ctypes.c_char_p
+    L.msa_version.restype = ctypes.c_char_p
+    L.msa_set_stream.argtypes = [ctypes.c_void_p]
+    L.msa_config.argtypes = [ctypes.c_char_p, ctypes.c_int64]
+    L.msa_plan_create.argtypes = [ctypes.c_int, i32p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
+    L.msa_plan_execute.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.msa_plan_get_info.argtypes = [ctypes.c_void_p, ctypes.POINTER(PlanInfo)]
+    L.msa_plan_destroy.argtypes = [ctypes.c_void_p]
+    L.msa_plan_read_tb.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+    L.msa_plan_timings.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]
+    L.msa_submit.argtypes = [ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.msa_poll.argtypes = [ctypes.c_uint64, i32p, ctypes.c_char_p]
+    L.msa_cancel.argtypes = [ctypes.c_uint64]
+    L.msa_wave_sizes.argtypes = [ctypes.c_int, i32p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, i32p]
+    L.msa_tile_shape.argtypes = [ctypes.c_int, i32p, i32p, i32p]
+    _lib = L
+    return L
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise MsaError(rc, library().msa_last_error().decode(errors="replace"))
+    return rc
+
+
+def last_error() -> str:
+    return library().msa_last_error().decode(errors="replace")
+
+
+def version() -> str:
+    return library().msa_version().decode()
+
+
+def _i32(values) -> ctypes.Array:
+    vals = [int(v) for v in values]
+    return (ctypes.c_int32 * max(1, len(vals)))(*vals)
+
+
+def _table(subst) -> ctypes.Array:
+    t = np.ascontiguousarray(np.asarray(subst, dtype=np.int64).reshape(-1))
+    return _i32(t.tolist())
+
+
+def _rows(buf: bytes, k: int, stride: int) -> List[str]:
+    out = []
+    for i in range(k):
+        row = buf[i * stride:(i + 1) * stride]
+        out.append(row.split(b"\0", 1)[0].decode())
+    return out
+
+
+def msa_align(seqs: Sequence[str], alphabet: str, subst, gap: int) -> Tuple[int, List[str]]:
+    """Optimal SP alignment through the synchronous C-ABI call (host buffers)."""
+    L = library()
+    k = len(seqs)
+    enc = [s.encode() for s in seqs]
+    arr = (ctypes.c_char_p * max(1, k))(*enc)
+    lens = _i32([len(s) for s in enc])
+    stride = sum(len(s) for s in enc) + 1
+    out = ctypes.create_string_buffer(k * stride)
+    score = ctypes.c_int32(0)
+    _check(L.msa_align(k, arr, lens, alphabet.encode(), _table(subst), int(gap), ctypes.byref(score), out))
+    return int(score.value), _rows(out.raw, k, stride)
+
+
+def msa_config(key: str, value: int) -> None:
+    _check(library().msa_config(key.encode(), int(value)))
+
+
+def msa_set_stream(stream_handle: Optional[int]) -> None:
+    _check(library().msa_set_stream(ctypes.c_void_p(stream_handle or 0)))
+
+
+def msa_wave_sizes(grid: Sequence[int]) -> List[int]:
+    L = library()
+    k = len(grid)
+    total = sum(int(g) for g in grid) + 1
+    out = (ctypes.c_int64 * total)()
+    nw = ctypes.c_int32(0)
+    _check(L.msa_wave_sizes(k, _i32(grid), out, total, ctypes.byref(nw)))
+    return [int(out[i]) for i in range(nw.value)]
+
+
+def msa_tile_shape(lens: Sequence[int]) -> Tuple[List[int], List[int]]:
+    L = library()
+    k = len(lens)
+    ext = (ctypes.c_int32 * MAX_K)()
+    grid = (ctypes.c_int32 * MAX_K)()
+    _check(L.msa_tile_shape(k, _i32(lens), ext, grid))
+    return list(ext[:k]), list(grid[:k])
+
+
+class Plan:
+    """A fixed problem shape with its device workspace (msa_plan_*)."""
+
+    def __init__(self, k: int, lens: Sequence[int], alphabet: str):
+        self._lib = library()
+        self.k = k
+        self.lens = [int(n) for n in lens]
+        self.alphabet = alphabet
+        h = ctypes.c_void_p()
+        _check(self._lib.msa_plan_create(k, _i32(self.lens), alphabet.encode(), ctypes.byref(h)))
+        self._h = h
+
+    def execute(self, d_residues: int, d_subst: int, gap: int, d_result: int, d_masks: int,
+                stream: Optional[int] = None) -> None:
+        """Launch the hot path on device pointers (asynchronous on ``stream``)."""
+        _check(self._lib.msa_plan_execute(self._h, ctypes.c_void_p(d_residues), ctypes.c_void_p(d_subst),
+                                          int(gap), ctypes.c_void_p(d_result), ctypes.c_void_p(d_masks),
+                                          ctypes.c_void_p(stream or 0)))
+
+    def info(self) -> PlanInfo:
+        inf = PlanInfo()
+        _check(self._lib.msa_plan_get_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    def read_tb(self) -> np.ndarray:
+        """The traceback tensor of the last execution, unpadded, shape (len_i + 1)."""
+        inf = self.info()
+        raw = np.empty(int(inf.tb_bytes), dtype=np.uint8)
+        _check(self._lib.msa_plan_read_tb(self._h, raw.ctypes.data, int(inf.tb_bytes)))
+        shape = tuple(n + 1 for n in self.lens)
+        strides = tuple(int(inf.tb_strides[i]) for i in range(self.k))
+        return np.lib.stride_tricks.as_strided(raw, shape=shape, strides=strides).copy()
+
+    def timings(self) -> Tuple[float, float, float]:
+        """(encode, fill, traceback) milliseconds of the last timed execution."""
+        out = (ctypes.c_float * 3)()
+        _check(self._lib.msa_plan_timings(self._h, out))
+        return float(out[0]), float(out[1]), float(out[2])
+
+    def close(self) -> None:
+        if self._h:
+            self._lib.msa_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def msa_submit(seqs: Sequence[str], alphabet: str, subst, gap: int) -> int:
+    L = library()
+    k = len(seqs)
+    enc = [s.encode() for s in seqs]
+    req = Request(k, (ctypes.c_char_p * max(1, k))(*enc), _i32([len(s) for s in enc]), alphabet.encode(),
+                  _table(subst), int(gap))
+    h = ctypes.c_uint64(0)
+    _check(L.msa_submit(ctypes.byref(req), ctypes.byref(h)))
+    return int(h.value)
+
+
+def msa_poll(handle: int, k: int, total_len: int) -> Optional[Tuple[int, List[str]]]:
+    """None while pending; (score, rows) when done; raises MsaError on failure."""
+    L = library()
+    stride = total_len + 1
+    out = ctypes.create_string_buffer(k * stride)
+    score = ctypes.c_int32(0)
+    rc = L.msa_poll(ctypes.c_uint64(handle), ctypes.byref(score), out)
+    if rc == MSA_PENDING:
+        return None
+    _check(rc)
+    return int(score.value), _rows(out.raw, k, stride)
+
+
+def msa_cancel(handle: int) -> None:
+    _check(library().msa_cancel(ctypes.c_uint64(handle)))
+
+
+def msa_drain() -> None:
+    _check(library().msa_drain())
+
+
+# ---------------------------------------------------------------------------
+# torch helpers: device tensors in, device tensors out (marshalling only).
+
+def device_inputs(problem, device="cuda"):
+    """Residues (uint8) and table (int32) of a problem as device tensors."""
+    import torch
+    res = np.frombuffer("".join(problem.seqs).encode(), dtype=np.uint8).copy()
+    d_res = torch.from_numpy(res).to(device) if res.size else torch.zeros(1, dtype=torch.uint8, device=device)
+    d_sub = torch.from_numpy(np.ascontiguousarray(problem.subst, dtype=np.int32).reshape(-1)).to(device)
+    return d_res, d_sub
+
+
+def device_outputs(total_len: int, device="cuda"):
+    import torch
+    d_result = torch.zeros(4, dtype=torch.int32, device=device)
+    d_masks = torch.zeros(max(1, total_len), dtype=torch.uint8, device=device)
+    return d_result, d_masks
+
+
+def decode_device_result(d_result, d_masks, seqs: Sequence[str]) -> Tuple[int, List[str], int]:
+    """(score, rows, status) from the device result block and reversed masks."""
+    r = d_result.cpu().tolist()
+    score, ncols, status = r[0], r[1], r[2]
+    if status != 0:
+        return score, [], status
+    masks = d_masks[:ncols].cpu().numpy()[::-1]
+    pos = [0] * len(seqs)
+    rows = [[] for _ in seqs]
+    for m in masks:
+        for i, s in enumerate(seqs):
+            if (int(m) >> i) & 1:
+                rows[i].append(s[pos[i]])
+                pos[i] += 1
+            else:
+                rows[i].append("-")
+    return score, ["".join(r) for r in rows], status
