@@ -38,7 +38,7 @@ import inputs  # noqa: E402
 METRIC = "DP cells/s"
 UNIT = "cells/s"
 SMS_GB300 = 152
-INT32_LANES_PER_SM = 64   # 4 SM sub-partitions x 16 INT32 lanes
+INT32_LANES_PER_SM = 128  # 4 SM sub-partitions x 32 lanes: IADD/IMNMX issue at full rate (measured)
 SM_MAX_MHZ_FALLBACK = 2070.0
 
 

@@ -113,15 +113,16 @@ int device_sm_count() {
     return sms;
 }
 
-int persistent_grid(int k, int kernel, int64_t units) {
-    static int cache[3][MSA_MAX_K + 1] = {};
-    int &c = cache[kernel][k];
+int persistent_grid(int k, int kernel, int64_t units, int A) {
+    static int cache[3][MSA_MAX_K + 1][MSA_MAX_ALPHABET + 1] = {};
+    int &c = cache[kernel][k][kernel == kKernelCol3 ? A : 0];
     if (!c) {
-        c = kernel == kKernelCol3 ? fill_col3_ctas_per_sm() : fill_tiles_ctas_per_sm(k);
+        c = kernel == kKernelCol3 ? fill_col3_ctas_per_sm(col3_smem_bytes(A)) : fill_tiles_ctas_per_sm(k);
         if (c <= 0) c = 1;
     }
-    const int warps = kernel == kKernelCol3 ? col3_warps_per_cta() : tiles_warps_per_cta(k);
-    int64_t need = (units + warps - 1) / warps;
+    // the tile kernel takes one unit per warp, the column kernel one per CTA
+    const int per_cta = kernel == kKernelCol3 ? 1 : tiles_warps_per_cta(k);
+    int64_t need = (units + per_cta - 1) / per_cta;
     int64_t g = (int64_t)c * device_sm_count();
     if (need < g) g = need;
     return (int)(g < 1 ? 1 : g);
@@ -187,6 +188,11 @@ void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_
     }
     d.tile_base = tile_base;
     d.ntiles = hp.ntiles;
+    d.has_qcorner = hp.kernel == kKernelTiles ? 1 : 0;
+    d.face0_stride = hp.face0_stride;
+    d.face1_stride = hp.face1_stride;
+    d.face0_rows = hp.face0_rows;
+    d.face1_rows = hp.face1_rows;
     d.pair_min_sum = hp.pair_min_sum;
     d.w_corner = hp.w_corner;
     d.len_sum = hp.len_sum;
@@ -201,7 +207,7 @@ void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_
 }
 
 int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t s) {
-    cudaError_t e = hp.kernel == kKernelCol3 ? launch_fill_col3(L, grid, s)
+    cudaError_t e = hp.kernel == kKernelCol3 ? launch_fill_col3(L, grid, col3_smem_bytes(hp.A), s)
                                              : launch_fill_tiles(hp.k, L, grid, s);
     return e == cudaSuccess ? MSA_OK : cuda_error(e, "fill kernel launch");
 }
@@ -309,7 +315,7 @@ int msa_plan_create(int k, const int32_t *lens, const char *alphabet, msa_plan *
         delete p;
         return cuda_error(e, "plan upload");
     }
-    p->grid = persistent_grid(k, p->hp.kernel, p->hp.ntiles);
+    p->grid = persistent_grid(k, p->hp.kernel, p->hp.ntiles, A);
     *out_plan = p;
     return MSA_OK;
 }
@@ -353,6 +359,7 @@ int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_su
     L.spin_ns = spin_ms * 1000000LL;
     L.withhold = withhold;
     L.nprob = 1;
+    L.tab_ints = plan->hp.A * plan->hp.A * 32;
     if (ev) cudaEventRecord(ev[1], s);
     int rc = launch_fill(plan->hp, L, plan->grid, s);
     if (rc) return rc;
@@ -439,7 +446,7 @@ size_t g_host_io_bytes = 0;
 
 bool same_shape(const msa_plan *p, int k, const int32_t *lens, const char *alphabet, int kernel) {
     if (!p || p->hp.k != k || strcmp(p->alphabet, alphabet) != 0) return false;
-    if (kernel != kKernelAuto && p->hp.kernel != choose_kernel(k, lens, kernel)) return false;
+    if (p->hp.kernel != choose_kernel(k, lens, p->hp.A, kernel)) return false;
     for (int i = 0; i < k; ++i)
         if (p->hp.lens[i] != lens[i]) return false;
     return true;

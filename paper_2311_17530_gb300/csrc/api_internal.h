@@ -55,7 +55,7 @@ int validate_alphabet(const char *alphabet, uint8_t amap[256]);
 int validate_request(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
                      const int32_t *subst, uint8_t amap[256]);
 int status_error(int status);
-int persistent_grid(int k, int kernel, int64_t units);
+int persistent_grid(int k, int kernel, int64_t units, int A);
 size_t plan_layout(const HostPlan &hp, char *base, PlanPointers *pp, size_t *reset_bytes);
 void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_base, ProblemDesc &d);
 int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t s);

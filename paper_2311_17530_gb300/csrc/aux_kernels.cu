@@ -26,32 +26,35 @@ __global__ void encode_kernel(const ProblemDesc *probs, const IODesc *io_arr, IO
     }
     __syncthreads();
     const int A = P.A, B = P.B;
-    int lmax = 0, lbad = 0;
+    int lmax = 0, lbad = 0, lbig = 0;
     for (int i = threadIdx.x; i < A * A; i += blockDim.x) {
         const int a = i / A, b = i - a * A;
         const int64_t v = io.subst[i];
         if (v != (int64_t)io.subst[b * A + a]) lbad = 1;
-        const int64_t pp = v - 2 * (int64_t)io.gap;
+        const int64_t pp = v - 2 * (int64_t)io.gap;  // pair score with the gap terms folded in
         const int64_t ap = pp < 0 ? -pp : pp;
-        if (ap > (1 << 20)) {
-            lmax = 1 << 21;
+        if ((ap << B) >= kKeyLimit) {
+            lbig = 1;
             P.tab[i] = 0;
         } else {
             lmax = max(lmax, (int)ap);
-            P.tab[i] = (int32_t)(pp * (1 << B));
+            P.tab[i] = (int32_t)(pp * ((int64_t)1 << B));
         }
     }
     atomicMax(&smax, lmax);
     if (lbad) atomicOr(&sbad, 1);
+    if (lbig) atomicOr(&sbad, 2);
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (sbad) atomicCAS(&st->status, 0, MSA_EINVAL);
+        if (sbad & 1) atomicCAS(&st->status, 0, MSA_EINVAL);
+        // |H'| <= maxp * sum_{i<j} min(len_i, len_j); a candidate adds at most
+        // C(k,2) * maxp; keys carry the factor 2^B and the potential W <= W(len).
         const int64_t npairs = (int64_t)P.k * (P.k - 1) / 2;
         const int64_t key_bound =
             (int64_t)smax * (P.pair_min_sum + npairs) * ((int64_t)1 << B) + P.w_corner;
         const int64_t g = io.gap < 0 ? -(int64_t)io.gap : (int64_t)io.gap;
         const int64_t score_bound = (int64_t)smax * P.pair_min_sum + g * (P.k - 1) * P.len_sum;
-        if (key_bound >= kKeyLimit || score_bound >= ((int64_t)1 << 31) - 1)
+        if ((sbad & 2) || key_bound >= kKeyLimit || score_bound >= ((int64_t)1 << 31) - 1)
             atomicCAS(&st->status, 0, MSA_ETOOBIG);
     }
 }
@@ -67,10 +70,22 @@ cudaError_t launch_encode(const ProblemDesc *d_probs, int nprob, int max_ncode,
 
 // Traceback (section 2): from the far corner follow the stored move of every
 // cell back to the origin. One warp per problem: the warp stages the box
-// [x - D, x] of the traceback tensor into shared memory with coalesced 4-byte
-// loads, lane 0 walks the path inside the box until it leaves through a lower
-// face, and the next box is staged around the new position. The masks are
-// written last column first; the score is decoded from the corner's packed key.
+// [x - D, x] of the traceback tensor into shared memory with asynchronous
+// global->shared copies (all issued, then one wait), lane 0 walks the path inside
+// the box until it leaves through a lower face, and the next box is staged
+// around the new position. Boxes are aligned to the copy granule along the last
+// axis. The masks are written last column first; the score is decoded from the
+// corner's packed key.
+__device__ __forceinline__ void cp_async_16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __global__ void __launch_bounds__(32) traceback_kernel(const ProblemDesc *probs, const int32_t *err,
                                                        const IODesc *io_arr, IODesc io1) {
     const int p = blockIdx.x;
@@ -90,9 +105,19 @@ __global__ void __launch_bounds__(32) traceback_kernel(const ProblemDesc *probs,
     }
     const int K = P.k, B = P.B;
     const int D = traceback_box(K);
+    const int G = traceback_granule(K);  // bytes per copy: 16 (k <= 4) or 4
+    const int A = P.A;
     int x[MSA_MAX_K], lo[MSA_MAX_K], ext[MSA_MAX_K];
-    int64_t bs[MSA_MAX_K];
-    for (int i = 0; i < K; ++i) x[i] = P.len[i];
+    int64_t bs[MSA_MAX_K], ts[MSA_MAX_K];
+    for (int i = 0; i < K; ++i) {
+        x[i] = P.len[i];
+        ts[i] = P.tbstride[i];
+    }
+    // The score is the sum of the traced columns' SP scores: with the gap terms
+    // folded in, a column of move m scores u*|m| + sum_{i<j in m} (sub - 2 gap),
+    // u = gap * (k - 1), and tab holds (sub - 2 gap) << k.
+    const int u = io.gap * (K - 1);
+    int score = 0;
     int ncols = 0;
     int fail = 0;
     while (true) {
@@ -100,29 +125,34 @@ __global__ void __launch_bounds__(32) traceback_kernel(const ProblemDesc *probs,
         for (int i = 0; i < K; ++i) any = any || x[i] > 0;
         if (!any || fail) break;
         for (int i = 0; i < K; ++i) lo[i] = max(0, x[i] - D);
-        const int a = lo[K - 1] & ~3;
-        const int rowb = round_up(x[K - 1] - a + 1, 4);
+        const int a = lo[K - 1] & ~(G - 1);
+        const int rowb = round_up(x[K - 1] - a + 1, G);
+        const int cpr = rowb / G;  // copies per row
         bs[K - 1] = 1;
         int64_t stride = rowb;
+        int rows = 1;
         for (int i = K - 2; i >= 0; --i) {
             bs[i] = stride;
             ext[i] = x[i] - lo[i] + 1;
             stride *= ext[i];
+            rows *= ext[i];
         }
-        const int wpr = rowb / 4;
-        const int words = (int)(stride / 4);
-        for (int w = lane; w < words; w += 32) {
-            const int row = w / wpr, cw = w - row * wpr;
+        for (int row = lane; row < rows; row += 32) {
             int r = row;
-            int64_t g = a + 4 * cw;
+            int64_t g = a;
             for (int i = K - 2; i >= 0; --i) {
                 const int ci = r % ext[i];
                 r /= ext[i];
-                g += (int64_t)(lo[i] + ci) * P.tbstride[i];
+                g += (int64_t)(lo[i] + ci) * ts[i];
             }
-            const uint32_t v = __ldcg(reinterpret_cast<const unsigned int *>(P.tb + g));
-            *reinterpret_cast<uint32_t *>(box + (int64_t)row * rowb + 4 * cw) = v;
+            unsigned char *dst = box + (int64_t)row * rowb;
+            const uint8_t *src = P.tb + g;
+            if (G == 16)
+                for (int c = 0; c < cpr; ++c) cp_async_16(dst + 16 * c, src + 16 * c);
+            else
+                for (int c = 0; c < cpr; ++c) cp_async_4(dst + 4 * c, src + 4 * c);
         }
+        cp_async_wait_all();
         __syncwarp();
         if (lane == 0) {
             int64_t li = x[K - 1] - a;
@@ -140,6 +170,17 @@ __global__ void __launch_bounds__(32) traceback_kernel(const ProblemDesc *probs,
                     break;
                 }
                 io.masks[ncols++] = (uint8_t)m;
+                // column score: residues entering x (position x_i - 1 of each moved sequence)
+                int c[MSA_MAX_K];
+                int nm = 0;
+                for (int i = 0; i < K; ++i)
+                    if ((m >> i) & 1) {
+                        c[nm++] = P.codes[P.cofs[i] + x[i] - 1];
+                    }
+                int col = u * nm;
+                for (int i = 0; i < nm; ++i)
+                    for (int j = i + 1; j < nm; ++j) col += P.tab[c[i] * A + c[j]] >> B;
+                score += col;
                 bool out = false;
                 for (int i = 0; i < K; ++i)
                     if ((m >> i) & 1) {
@@ -156,9 +197,13 @@ __global__ void __launch_bounds__(32) traceback_kernel(const ProblemDesc *probs,
         __syncwarp();
     }
     if (lane == 0) {
-        const int q = *P.qcorner;
-        const int hprime = (q - P.w_corner) >> B;  // exact: q = H' * 2^B + W(corner)
-        io.result->score = hprime + io.gap * (K - 1) * P.len_sum;
+        if (!fail && P.has_qcorner) {
+            // cross-check against the fill's own corner value: q = H' * 2^B + W(corner)
+            const int q = *P.qcorner;
+            const int h = ((q - P.w_corner) >> B) + u * P.len_sum;
+            if (h != score) fail = 1;
+        }
+        io.result->score = score;
         io.result->ncols = ncols;
         io.result->status = fail ? MSA_ECUDA : MSA_OK;
     }

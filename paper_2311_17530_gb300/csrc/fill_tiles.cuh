@@ -158,25 +158,38 @@ fill_tiles_kernel(const LaunchDesc L) {
                         (x >= 1 && x <= len[j]) ? codes[cofs[j] + x - 1] : (uint8_t)0;
                 }
 
-            // Halo: every cell with some local coordinate -1, face by face.
+            // Halo: every cell with some local coordinate -1, face by face. Loads
+            // bypass L1 (other SMs wrote these cells) and are issued in batches of
+            // HB before their shared-memory stores, so a face costs about one L2
+            // round trip per batch rather than one per element.
+            constexpr int HB = 8;
 #pragma unroll
             for (int f = 0; f < K; ++f) {
-                for (int i = lane; i < face_size(K, f); i += 32) {
-                    int r = i, soff = 0;
-                    bool in = true, neg = false;
-                    int64_t g = 0;
+                for (int i0 = 0; i0 < face_size(K, f); i0 += 32 * HB) {
+                    int val[HB], dst[HB];
 #pragma unroll
-                    for (int j = 0; j < K; ++j) {
-                        const int fs = face_stride(K, f, j);
-                        int cj = r / fs;
-                        r -= cj * fs;
-                        if (j >= f) cj -= 1;
-                        in = in && (cj < e[j]);
-                        neg = neg || (cj < 0 && o[j] == 0);
-                        soff += (cj + 1) * geo_sh(K, j);
-                        g += (int64_t)(o[j] + cj) * qstr[j];
+                    for (int u = 0; u < HB; ++u) {
+                        const int i = i0 + 32 * u + lane;
+                        int r = i, soff = 0;
+                        bool in = i < face_size(K, f), neg = false;
+                        int64_t g = 0;
+#pragma unroll
+                        for (int j = 0; j < K; ++j) {
+                            const int fs = face_stride(K, f, j);
+                            int cj = r / fs;
+                            r -= cj * fs;
+                            if (j >= f) cj -= 1;
+                            in = in && (cj < e[j]);
+                            neg = neg || (cj < 0 && o[j] == 0);
+                            soff += (cj + 1) * geo_sh(K, j);
+                            g += (int64_t)(o[j] + cj) * qstr[j];
+                        }
+                        dst[u] = in ? soff : -1;
+                        val[u] = (in && !neg) ? __ldcg(Qg + g) : kNeg;
                     }
-                    if (in) qs[soff] = neg ? kNeg : __ldcg(Qg + g);
+#pragma unroll
+                    for (int u = 0; u < HB; ++u)
+                        if (dst[u] >= 0) qs[dst[u]] = val[u];
                 }
             }
             __syncwarp();

@@ -44,7 +44,11 @@ struct ProblemDesc {
     int32_t pair_min_sum;        // sum_{i<j} min(len_i, len_j): bound on pair moves
     int32_t w_corner;            // W(len)
     int32_t len_sum;
-    int32_t pad0;
+    int32_t has_qcorner;         // the fill records the corner's packed key (cross-check)
+    int64_t face0_stride;        // column kernel: ints per column in Q (axis-0 faces)
+    int64_t face1_stride;        // column kernel: ints per column in aux (axis-1 faces)
+    int32_t face0_rows;          // column kernel: skewed rows per axis-0 face
+    int32_t face1_rows;          // column kernel: skewed rows per axis-1 face
     const uint8_t *amap;         // device 256-entry char -> code map (0xFF: invalid)
     uint8_t *codes;              // device codes
     int32_t *tab;                // device scaled pair table ((sub - 2 gap) << B)
@@ -77,7 +81,7 @@ struct LaunchDesc {
     int64_t spin_ns;         // limit of one dependency wait
     int64_t withhold;        // test hook: this ticket never publishes (-1: off)
     int32_t nprob;
-    int32_t pad;
+    int32_t tab_ints;        // column kernel: shared-memory ints of the replicated table
 };
 
 // Tile extents of the generic kernel, per k (compile-time in the kernel).
@@ -90,11 +94,37 @@ __host__ __device__ constexpr int tile_extent(int k, int i) {
          : 2;
 }
 
-// Traceback box edge per k (box of (D+1)^k cells staged in shared memory).
-__host__ __device__ constexpr int traceback_box(int k) {
-    return k == 2 ? 200 : k == 3 ? 32 : k == 4 ? 12 : k == 5 ? 7 : k == 6 ? 4 : k == 7 ? 3 : 2;
+// k = 3 column kernel geometry (shared by the planner and the kernel).
+namespace c3 {
+constexpr int R = 8;         // rows per warp along axis 0 (registers)
+constexpr int W = 8;         // warps per CTA, stacked along axis 0
+constexpr int WR = R * W;    // rows per CTA
+constexpr int CH = 12;       // lockstep steps per chunk (staging + progress granularity)
+constexpr int S = 32;        // shared ring slots
+constexpr int THREADS = 32 * W;
+constexpr int MAXA = 24;     // largest alphabet (replicated pair table)
+constexpr int MAXRHO2 = 4096;  // largest axis-2 extent (staged codes)
+constexpr int EXTRA = 8;     // sweep steps past the last position (flushes packed words)
+constexpr int CODEPAD = 64;  // axis-2 code staging pad on both sides
+// lockstep steps of one column: sweep TS = rho2 + R + 31 + EXTRA per warp, warps
+// lagging R steps each, rounded up to whole chunks
+__host__ __device__ constexpr int nsteps(int rho2) {
+    return ((rho2 + R + 31 + EXTRA + (W - 1) * R) + CH - 1) / CH * CH;
 }
-constexpr int kTracebackSmem = 48 * 1024;
+__host__ __device__ constexpr int face0_rows(int rho2) { return nsteps(rho2) + CH; }
+__host__ __device__ constexpr int face1_rows(int rho2) { return nsteps(rho2) + WR + CH; }
+}  // namespace c3
+
+// Traceback box edge D per k (the box [x-D, x] is staged in shared memory; rows
+// along the last axis are copied in granules of traceback_granule(k) bytes, so a
+// staged row holds at most round_up(D + granule, granule) bytes).
+__host__ __device__ constexpr int traceback_box(int k) {
+    return k == 2 ? 192 : k == 3 ? 28 : k == 4 ? 11 : k == 5 ? 7 : k == 6 ? 4 : k == 7 ? 3 : 2;
+}
+__host__ __device__ constexpr int traceback_granule(int k) { return k <= 4 ? 16 : 4; }
+constexpr int kTracebackSmem = 72 * 1024;
+// The traceback tensor's last axis is padded to this many bytes (16-byte rows).
+constexpr int kTbRowAlign = 16;
 
 // Kernel entry points (host wrappers), defined in the .cu files.
 // A kernel reads its per-problem IODesc from io_array[p] when io_array is set,
@@ -103,8 +133,9 @@ cudaError_t launch_encode(const ProblemDesc *d_probs, int nprob, int max_ncode,
                           const IODesc *io_array, IODesc io_single, cudaStream_t s);
 cudaError_t launch_fill_tiles(int k, const LaunchDesc &L, int grid, cudaStream_t s);
 int fill_tiles_ctas_per_sm(int k);
-cudaError_t launch_fill_col3(const LaunchDesc &L, int grid, cudaStream_t s);
-int fill_col3_ctas_per_sm();
+cudaError_t launch_fill_col3(const LaunchDesc &L, int grid, int smem, cudaStream_t s);
+int fill_col3_ctas_per_sm(int smem);
+int col3_smem_bytes(int alphabet_size);
 cudaError_t launch_traceback(const ProblemDesc *d_probs, int nprob, const int32_t *err,
                              const IODesc *io_array, IODesc io_single, cudaStream_t s);
 

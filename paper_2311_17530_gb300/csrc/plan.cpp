@@ -10,16 +10,28 @@
 
 namespace msadp {
 
-int choose_kernel(int k, const int32_t *lens, int requested) {
-    (void)lens;
-    if (requested == kKernelCol3) return k == 3 ? kKernelCol3 : kKernelTiles;
+// The k = 3 column kernel handles alphabets up to c3::MAXA, a last axis up to
+// c3::MAXRHO2, and keeps per-row traceback offsets in 32 bits.
+static bool col3_fits(int k, const int32_t *lens, int A) {
+    if (k != 3 || A > c3::MAXA) return false;
+    const int64_t rho2 = (int64_t)lens[2] + 1;
+    const int64_t row = (rho2 + kTbRowAlign - 1) / kTbRowAlign * kTbRowAlign;
+    return rho2 <= c3::MAXRHO2 && ((int64_t)lens[1] + 1) * row * c3::R < (1LL << 31);
+}
+
+int choose_kernel(int k, const int32_t *lens, int A, int requested) {
     if (requested == kKernelTiles) return kKernelTiles;
+    if (col3_fits(k, lens, A)) return kKernelCol3;
     return kKernelTiles;
 }
 
 void tile_extents(int k, const int32_t *lens, int kernel, int32_t *E) {
-    (void)lens;
-    (void)kernel;
+    if (kernel == kKernelCol3) {
+        E[0] = c3::WR;
+        E[1] = 32;
+        E[2] = lens[2] + 1;
+        return;
+    }
     for (int i = 0; i < k; ++i) E[i] = tile_extent(k, i);
 }
 
@@ -58,7 +70,7 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
     hp = HostPlan();
     hp.k = k;
     hp.A = A;
-    hp.kernel = choose_kernel(k, lens, kernel_choice);
+    hp.kernel = choose_kernel(k, lens, A, kernel_choice);
     long double cells = 1;
     int64_t len_sum = 0, w_corner = 0, pair_min = 0;
     for (int i = 0; i < k; ++i) {
@@ -107,13 +119,35 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
         s *= (i == k - 1) ? round_up64(hp.rho[i], 4) : hp.rho[i];
     }
     hp.qelems = s;
-    // traceback tensor: row-major, last axis padded to 4 bytes
+    // traceback tensor: row-major, last axis padded to 16-byte rows
     s = 1;
     for (int i = k - 1; i >= 0; --i) {
         hp.tbstride[i] = s;
-        s *= (i == k - 1) ? round_up64(hp.rho[i], 4) : hp.rho[i];
+        s *= (i == k - 1) ? round_up64(hp.rho[i], kTbRowAlign) : hp.rho[i];
     }
     hp.tbbytes = s;
+
+    if (hp.kernel == kKernelCol3) {
+        // faces between columns and the column order: a column (a, b) can start
+        // about a*(WR + 2 CH) + b*(32 + 2 CH) lockstep steps after the first, so
+        // tickets follow that estimate (every producer gets a smaller ticket)
+        const int rho2 = hp.rho[2];
+        hp.face0_rows = c3::face0_rows(rho2);
+        hp.face1_rows = c3::face1_rows(rho2);
+        hp.face0_stride = (int64_t)hp.face0_rows * 32;
+        hp.face1_stride = (int64_t)hp.face1_rows * c3::WR;
+        hp.qelems = nt * hp.face0_stride;
+        hp.aux_elems = nt * hp.face1_stride;
+        std::vector<std::pair<int64_t, int64_t>> key(nt);
+        for (int64_t t = 0; t < nt; ++t) {
+            const int64_t a = t / hp.G[1], b = t % hp.G[1];
+            key[t] = {a * (c3::WR + 2 * c3::CH) + b * (32 + 2 * c3::CH), t};
+        }
+        std::sort(key.begin(), key.end());
+        hp.order.resize(nt);
+        for (int64_t t = 0; t < nt; ++t) hp.order[t] = (uint64_t)key[t].second;
+        return MSA_OK;
+    }
 
     // ticket order: by wave, then by linear tile index (counting sort)
     std::vector<int64_t> cnt(hp.waves + 1, 0);

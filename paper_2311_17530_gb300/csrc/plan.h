@@ -27,6 +27,10 @@ struct HostPlan {
     int64_t qstride[MSA_MAX_K] = {};
     int64_t qelems = 0;            // score scratch elements
     int64_t aux_elems = 0;         // second scratch array (column kernel)
+    int64_t face0_stride = 0;      // column kernel face layout
+    int64_t face1_stride = 0;
+    int32_t face0_rows = 0;
+    int32_t face1_rows = 0;
     int64_t tbstride[MSA_MAX_K] = {};
     int64_t tbbytes = 0;
     int32_t pair_min_sum = 0;
@@ -45,6 +49,6 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
 void wave_sizes(int k, const int32_t *grid, std::vector<int64_t> &out);
 
 // Which fill kernel runs for this shape when the caller leaves the choice open.
-int choose_kernel(int k, const int32_t *lens, int requested);
+int choose_kernel(int k, const int32_t *lens, int A, int requested);
 
 }  // namespace msadp

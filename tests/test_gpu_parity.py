@@ -143,7 +143,11 @@ def test_device_side_input_errors():
     asym[0, 1] = 2
     d_asym = torch.from_numpy(asym.reshape(-1).astype(np.int32)).cuda()
     assert run_plan(p, subst=d_asym)[2] == msa.MSA_EINVAL
-    huge = torch.from_numpy((p.subst * 100000).reshape(-1).astype(np.int32)).cuda()
+    # x10^5 still fits the packed int32 keys for these short sequences: exact result
+    scaled = inputs.Problem(p.name, p.seqs, p.alphabet, p.subst * 100000, p.gap * 100000)
+    check_problem(scaled)
+    # x10^7 does not: the device range check refuses it instead of overflowing
+    huge = torch.from_numpy((p.subst * 10**7).reshape(-1).astype(np.int32)).cuda()
     assert run_plan(p, subst=huge)[2] == msa.MSA_ETOOBIG
     # the context is still usable and the same plan shape works again
     check_problem(p)
@@ -163,3 +167,27 @@ def test_dependency_wait_timeout_is_reported_not_hung():
         msa.msa_config("test_withhold_tile", -1)
         msa.msa_config("spin_timeout_ms", 5000)
     check_problem(p)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_k3_both_fill_kernels_block_boundaries(kernel):
+    """k=3 through the generic tile kernel (1) and the column kernel (2): shapes
+    straddling the column kernel's 64-row CTA blocks, 32-lane blocks and chunks."""
+    msa.msa_config("fill_kernel", kernel)
+    try:
+        shapes = [(63, 31, 40), (64, 32, 100), (65, 33, 7), (130, 70, 50), (1, 1, 200),
+                  (200, 1, 1), (0, 100, 100), (100, 0, 5), (3, 3, 0), (129, 97, 61)]
+        for i, lens in enumerate(shapes):
+            p = inputs.random_problem(900 + i, 3, list(lens),
+                                      alphabet=inputs.PROTEIN if i % 2 else inputs.DNA, related=i % 3 == 0)
+            with msa.Plan(3, p.lens, p.alphabet) as plan:
+                assert plan.info().fill_kernel == kernel
+            check_problem(p)
+    finally:
+        msa.msa_config("fill_kernel", 0)
+
+
+def test_k3_auto_picks_column_kernel():
+    p = inputs.k3_protein()
+    with msa.Plan(3, [10, 10, 10], p.alphabet) as plan:
+        assert plan.info().fill_kernel == 2
