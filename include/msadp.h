@@ -175,6 +175,27 @@ int msa_plan_read_tb(msa_plan *plan, void *host_dst, int64_t bytes);
  */
 int msa_plan_timings(msa_plan *plan, float out_ms[3]);
 
+/*
+ * One alignment without any memory allocation (no counterpart in the paper; a
+ * library facility). For callers that must not call cudaMalloc: code running
+ * while another allocator owns the GPU's memory, latency-critical loops where an
+ * allocation would stall, callers that cannot recover from an allocation failure
+ * mid-request. Inputs, outputs and asynchrony are those of msa_plan_execute
+ * (d_residues, d_subst, d_result, d_masks are the caller's device buffers); all
+ * working memory is a fixed array of MSA_NOALLOC_SCRATCH_BYTES compiled into the
+ * library, held by every GPU that loads it until the process exits. Problems
+ * whose working set exceeds it (about 6 million cells) return MSA_ETOOBIG with
+ * the size they would need. The first call on each device looks up the array's
+ * device address; make that first call before any stream capture. Every call
+ * reuses the same array: calls whose GPU work overlaps (different streams or
+ * threads) race on it and must be serialised by the caller. Always uses the
+ * generic tile fill.
+ */
+#define MSA_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int msa_align_noalloc(int k, const int32_t *lens, const char *alphabet, const char *d_residues,
+                      const int32_t *d_subst, int32_t gap, msa_device_result *d_result, uint8_t *d_masks,
+                      void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of independent requests.                     */
 /* ------------------------------------------------------------------------ */

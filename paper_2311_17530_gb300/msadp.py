@@ -31,7 +31,7 @@ _NAMES = {MSA_EINVAL: "MSA_EINVAL", MSA_ETOOBIG: "MSA_ETOOBIG", MSA_ENOMEM: "MSA
 EXPORTED = ["msa_align", "msa_last_error", "msa_set_stream", "msa_config", "msa_plan_create",
             "msa_plan_execute", "msa_plan_get_info", "msa_plan_destroy", "msa_submit", "msa_poll",
             "msa_cancel", "msa_drain", "msa_wave_sizes", "msa_tile_shape", "msa_version",
-            "msa_plan_read_tb", "msa_plan_timings"]
+            "msa_plan_read_tb", "msa_plan_timings", "msa_align_noalloc"]
 
 
 class MsaError(RuntimeError):
@@ -81,6 +81,8 @@ def library() -> ctypes.CDLL:
     L.msa_plan_destroy.argtypes = [ctypes.c_void_p]
     L.msa_plan_read_tb.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
     L.msa_plan_timings.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float)]
+    L.msa_align_noalloc.argtypes = [ctypes.c_int, i32p, ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     L.msa_submit.argtypes = [ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     L.msa_poll.argtypes = [ctypes.c_uint64, i32p, ctypes.c_char_p]
     L.msa_cancel.argtypes = [ctypes.c_uint64]
@@ -218,6 +220,18 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+def msa_align_noalloc(lens: Sequence[int], alphabet: str, d_residues: int, d_subst: int, gap: int,
+                      d_result: int, d_masks: int, stream: Optional[int] = None) -> None:
+    """One alignment on the library's fixed device scratch (no allocation).
+
+    For callers that must not allocate device memory; pointers are device
+    buffers as for Plan.execute. Asynchronous on ``stream``.
+    """
+    _check(library().msa_align_noalloc(len(lens), _i32(lens), alphabet.encode(), ctypes.c_void_p(d_residues),
+                                       ctypes.c_void_p(d_subst), int(gap), ctypes.c_void_p(d_result),
+                                       ctypes.c_void_p(d_masks), ctypes.c_void_p(stream or 0)))
 
 
 def msa_submit(seqs: Sequence[str], alphabet: str, subst, gap: int) -> int:
