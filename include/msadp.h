@@ -119,7 +119,9 @@ typedef struct msa_plan_info {
     int64_t tiles;
     int32_t waves;              /* tile hyperplanes (section 3.1, Eq. 2) */
     int32_t fill_kernel;        /* 1 generic tile kernel, 2 k=3 column kernel */
-    void   *d_tb;               /* device pointer of the uint8 traceback tensor */
+    void   *d_tb;               /* device pointer of the uint8 traceback tensor: row-major with
+                                   tb_strides for the tile kernel; for the k=3 column kernel a
+                                   column-blocked layout (msa_plan_read_tb returns row-major) */
 } msa_plan_info;
 
 /* Result block written on the device by msa_plan_execute. */
@@ -160,9 +162,10 @@ int msa_plan_get_info(const msa_plan *plan, msa_plan_info *out_info);
 int msa_plan_destroy(msa_plan *plan);
 
 /*
- * Copy the traceback tensor of the last execution to host memory
+ * Copy the traceback tensor of the last execution to host memory, row-major
  * (info.tb_bytes bytes, layout given by info.tb_strides; the move mask of every
- * cell, 0 at the origin). Synchronises the plan's last stream. Diagnostic use.
+ * cell, 0 at the origin), converting from the device layout if needed.
+ * Synchronises the plan's last stream. Diagnostic use.
  */
 int msa_plan_read_tb(msa_plan *plan, void *host_dst, int64_t bytes);
 

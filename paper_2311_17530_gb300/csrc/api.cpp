@@ -148,7 +148,7 @@ size_t plan_layout(const HostPlan &hp, char *base, PlanPointers *pp, size_t *res
     char *codes = take((size_t)hp.len_sum + 16);
     char *tab = take((size_t)hp.A * hp.A * 4);
     char *qc = take(16);
-    char *tb = take((size_t)hp.tbbytes + 16);
+    char *tb = take((size_t)hp.tb_dev_bytes + 16);
     char *Q = take((size_t)hp.qelems * 4 + 16);
     char *aux = take((size_t)hp.aux_elems * 4 + 16);
     if (pp && base) {
@@ -193,6 +193,7 @@ void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_
     d.face1_stride = hp.face1_stride;
     d.face0_rows = hp.face0_rows;
     d.face1_rows = hp.face1_rows;
+    d.tb_layout = hp.tb_layout;
     d.pair_min_sum = hp.pair_min_sum;
     d.w_corner = hp.w_corner;
     d.len_sum = hp.len_sum;
@@ -204,6 +205,13 @@ void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_
     d.tb = pp.tb;
     d.qcorner = pp.qcorner;
     d.istat = &pp.state->istat;
+}
+
+cudaError_t clear_faces(const HostPlan &hp, const PlanPointers &pp, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(pp.Q, 0, (size_t)hp.qelems * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pp.aux, 0, (size_t)hp.aux_elems * 4, s);
+    if (e == cudaSuccess && s == nullptr) e = cudaDeviceSynchronize();
+    return e;
 }
 
 int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t s) {
@@ -223,6 +231,7 @@ struct msa_plan {
     PlanPointers pp;
     int grid = 1;
     cudaStream_t last_stream = nullptr;
+    int32_t epoch = 0;  // tag of the last execution's face entries (column kernel)
     // per-stage events of timed executions, a ring of kTimedRing executions
     static constexpr int kTimedRing = 256;
     std::vector<cudaEvent_t> ev;
@@ -310,6 +319,8 @@ int msa_plan_create(int k, const int32_t *lens, const char *alphabet, msa_plan *
     if (e == cudaSuccess)
         e = cudaMemcpy(p->pp.order, p->hp.order.data(), p->hp.order.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->pp.amap, amap, 256, cudaMemcpyHostToDevice);
+    // column kernel faces start with tag 0, which no execution uses
+    if (e == cudaSuccess && p->hp.kernel == kKernelCol3) e = clear_faces(p->hp, p->pp);
     if (e != cudaSuccess) {
         cudaFree(p->ws);
         delete p;
@@ -360,6 +371,14 @@ int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_su
     L.withhold = withhold;
     L.nprob = 1;
     L.tab_ints = plan->hp.A * plan->hp.A * 32;
+    if (plan->hp.kernel == kKernelCol3) {
+        if (plan->epoch >= (1 << 30)) {  // tags would wrap: start over from cleared faces
+            e = clear_faces(plan->hp, plan->pp, s);
+            if (e != cudaSuccess) return cuda_error(e, "face reset");
+            plan->epoch = 0;
+        }
+        L.epoch = ++plan->epoch;
+    }
     if (ev) cudaEventRecord(ev[1], s);
     int rc = launch_fill(plan->hp, L, plan->grid, s);
     if (rc) return rc;
@@ -396,11 +415,37 @@ int msa_plan_timings(msa_plan *plan, float out_ms[3]) {
 }
 
 int msa_plan_read_tb(msa_plan *plan, void *host_dst, int64_t bytes) {
-    if (!plan || !host_dst || bytes < 0 || bytes > plan->hp.tbbytes)
+    const HostPlan &hp = plan ? plan->hp : HostPlan();
+    if (!plan || !host_dst || bytes < 0 || bytes > hp.tbbytes)
         return set_error(MSA_EINVAL, "bad plan, destination or size");
     cudaError_t e = cudaStreamSynchronize(plan->last_stream);
-    if (e == cudaSuccess) e = cudaMemcpy(host_dst, plan->pp.tb, (size_t)bytes, cudaMemcpyDeviceToHost);
-    return e == cudaSuccess ? MSA_OK : cuda_error(e, "traceback tensor copy");
+    if (e != cudaSuccess) return cuda_error(e, "traceback tensor copy");
+    if (hp.tb_layout == 0) {
+        e = cudaMemcpy(host_dst, plan->pp.tb, (size_t)bytes, cudaMemcpyDeviceToHost);
+        return e == cudaSuccess ? MSA_OK : cuda_error(e, "traceback tensor copy");
+    }
+    // column-blocked device layout -> row-major host copy
+    std::vector<uint8_t> dev((size_t)hp.tb_dev_bytes);
+    e = cudaMemcpy(dev.data(), plan->pp.tb, dev.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "traceback tensor copy");
+    uint8_t *out = static_cast<uint8_t *>(host_dst);
+    const int rho2 = hp.rho[2];
+    const int64_t colb = c3::tb_col_bytes(rho2);
+    for (int x0 = 0; x0 < hp.rho[0]; ++x0) {
+        const int A = x0 / c3::WR, w = (x0 % c3::WR) / c3::R, r = x0 % c3::R;
+        for (int x1 = 0; x1 < hp.rho[1]; ++x1) {
+            const int B = x1 / 32, l = x1 % 32;
+            const uint8_t *col = dev.data() + (int64_t)(A * hp.G[1] + B) * colb;
+            const int64_t base = x0 * hp.tbstride[0] + x1 * hp.tbstride[1];
+            for (int x2 = 0; x2 < rho2; ++x2) {
+                const int64_t dst = base + x2;
+                if (dst >= bytes) continue;
+                const int t = x2 + l + r;
+                out[dst] = col[((int64_t)(t * c3::W + w) * 32 + l) * c3::R + r];
+            }
+        }
+    }
+    return MSA_OK;
 }
 
 int msa_plan_get_info(const msa_plan *plan, msa_plan_info *out) {

@@ -59,6 +59,7 @@ int persistent_grid(int k, int kernel, int64_t units, int A);
 size_t plan_layout(const HostPlan &hp, char *base, PlanPointers *pp, size_t *reset_bytes);
 void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_base, ProblemDesc &d);
 int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t s);
+cudaError_t clear_faces(const HostPlan &hp, const PlanPointers &pp, cudaStream_t s = nullptr);
 void expand_alignment(int k, const char *const *seqs, const int32_t *lens, const uint8_t *masks_rev,
                       int ncols, char *out);
 

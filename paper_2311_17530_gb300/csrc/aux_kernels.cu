@@ -86,6 +86,83 @@ __device__ __forceinline__ void cp_async_4(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Traceback over the k = 3 column kernel's layout. The walk stays inside one
+// column (A, B) as long as it can; the warp stages a window of that column --
+// lockstep steps [t - 24, t + 7], every warp block w, lanes [l0, l0 + 16) -- as
+// 8 x 16-byte runs per (step, w), and lane 0 walks inside it.
+constexpr int kTbcSteps = 32;   // steps per window
+constexpr int kTbcLanes = 16;   // lanes per window
+constexpr int kTbcBytes = kTbcSteps * c3::W * kTbcLanes * c3::R;  // 32 KB
+
+__device__ void traceback_col3(const ProblemDesc &P, const IODesc &io, unsigned char *box, int lane) {
+    const int nsym = P.A, bits = P.B;  // alphabet size, tie bits
+    const int u = io.gap * 2;  // gap * (k - 1)
+    const int NB = P.G[1];
+    const int rho2 = P.rho[2];
+    const int64_t colb = c3::tb_col_bytes(rho2);
+    int x0 = P.len[0], x1 = P.len[1], x2 = P.len[2];
+    int score = 0, ncols = 0, fail = 0;
+    while ((x0 | x1 | x2) != 0 && !fail) {
+        const int cA = x0 / c3::WR, cB = x1 >> 5;
+        const int l = x1 & 31, r = x0 & (c3::R - 1);
+        const int t = x2 + l + r;
+        const int t_lo = t - (kTbcSteps - 8);
+        const int l0 = max(0, l - (kTbcLanes - 2)) & ~1;  // even, and l0 <= l < l0 + 16
+        const unsigned char *col = P.tb + (int64_t)(cA * NB + cB) * colb;
+        // rows of the window: (step, w) pairs, 8 x 16 B each
+        for (int i = lane; i < kTbcSteps * c3::W * 8; i += 32) {
+            const int part = i & 7, row = i >> 3;
+            const int tt = t_lo + row / c3::W, w = row % c3::W;
+            if (tt >= 0 && tt < c3::sweep(rho2))
+                cp_async_16(box + row * (kTbcLanes * c3::R) + part * 16,
+                            col + ((int64_t)(tt * c3::W + w) * 32 + l0) * c3::R + part * 16);
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        if (lane == 0) {
+            const int before = ncols;
+            while ((x0 | x1 | x2) != 0) {
+                const int ca = x0 / c3::WR, cb = x1 >> 5;
+                const int ll = x1 & 31, rr = x0 & (c3::R - 1), ww = (x0 % c3::WR) >> 3;
+                const int tt = x2 + ll + rr;
+                if (ca != cA || cb != cB || ll < l0 || ll >= l0 + kTbcLanes || tt < t_lo || tt >= t_lo + kTbcSteps)
+                    break;
+                const int m = box[((tt - t_lo) * c3::W + ww) * (kTbcLanes * c3::R) + (ll - l0) * c3::R + rr];
+                if (m == 0 || m > 7 || ((m & 1) && x0 == 0) || ((m & 2) && x1 == 0) || ((m & 4) && x2 == 0) ||
+                    ncols >= P.len_sum) {
+                    fail = 1;
+                    break;
+                }
+                io.masks[ncols++] = (uint8_t)m;
+                // column score: u per residue plus the pair terms among moved sequences
+                int c[3], nm = 0;
+                if (m & 1) c[nm++] = P.codes[P.cofs[0] + x0 - 1];
+                if (m & 2) c[nm++] = P.codes[P.cofs[1] + x1 - 1];
+                if (m & 4) c[nm++] = P.codes[P.cofs[2] + x2 - 1];
+                int col_score = u * nm;
+                for (int i = 0; i < nm; ++i)
+                    for (int j = i + 1; j < nm; ++j) col_score += P.tab[c[i] * nsym + c[j]] >> bits;
+                score += col_score;
+                x0 -= m & 1;
+                x1 -= (m >> 1) & 1;
+                x2 -= (m >> 2) & 1;
+            }
+            if (ncols == before && (x0 | x1 | x2) != 0) fail = 1;  // a window must advance the walk
+        }
+        x0 = __shfl_sync(kFull, x0, 0);
+        x1 = __shfl_sync(kFull, x1, 0);
+        x2 = __shfl_sync(kFull, x2, 0);
+        ncols = __shfl_sync(kFull, ncols, 0);
+        fail = __shfl_sync(kFull, fail, 0);
+        __syncwarp();
+    }
+    if (lane == 0) {
+        io.result->score = score;
+        io.result->ncols = ncols;
+        io.result->status = fail ? MSA_ECUDA : MSA_OK;
+    }
+}
+
 __global__ void __launch_bounds__(32) traceback_kernel(const ProblemDesc *probs, const int32_t *err,
                                                        const IODesc *io_arr, IODesc io1) {
     const int p = blockIdx.x;
@@ -101,6 +178,10 @@ __global__ void __launch_bounds__(32) traceback_kernel(const ProblemDesc *probs,
             io.result->score = 0;
             io.result->ncols = 0;
         }
+        return;
+    }
+    if (P.tb_layout == 1) {
+        traceback_col3(P, io, box, lane);
         return;
     }
     const int K = P.k, B = P.B;
@@ -155,6 +236,7 @@ __global__ void __launch_bounds__(32) traceback_kernel(const ProblemDesc *probs,
         cp_async_wait_all();
         __syncwarp();
         if (lane == 0) {
+            const int before = ncols;
             int64_t li = x[K - 1] - a;
             for (int i = 0; i < K - 1; ++i) li += (int64_t)(x[i] - lo[i]) * bs[i];
             while (true) {
@@ -190,6 +272,9 @@ __global__ void __launch_bounds__(32) traceback_kernel(const ProblemDesc *probs,
                     }
                 if (out) break;
             }
+            bool left = false;
+            for (int i = 0; i < K; ++i) left = left || x[i] > 0;
+            if (ncols == before && left) fail = 1;  // a box must advance the walk
         }
         for (int i = 0; i < K; ++i) x[i] = __shfl_sync(kFull, x[i], 0);
         ncols = __shfl_sync(kFull, ncols, 0);

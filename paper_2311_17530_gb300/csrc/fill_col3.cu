@@ -15,114 +15,145 @@
 // one contiguous row:
 //   F0[cta][p + l][l]       last row of the CTA (x0 = A*WR + WR - 1) at x1 = 32B+l, x2 = p
 //   F1[cta][p + rho][rho]   last lane (x1 = 32B + 31) of CTA row rho at x2 = p
-// A CTA publishes how many of its lockstep steps are complete in a progress
-// counter; a consumer waits (bounded) until the producer is far enough ahead and
-// stages the next chunk of faces into shared memory with cp.async, one chunk
-// ahead of use.
+// Every face entry is a (value, tag) pair written by one 8-byte store; the tag is
+// the launch's epoch, so a reader knows an entry is current from the entry alone
+// (no flags, no fences). A ninth "staging" warp per CTA reads the faces its CTA
+// needs from its three producer CTAs, waits (bounded) until their tags are
+// current, and copies the values into shared rings up to AHEAD chunks ahead of
+// the eight compute warps, which only ever wait on a shared counter.
 //
 // Cell update (packed keys, see internal.h): with pair scores scaled by 2^3,
 //   Q(x) = max( Q(x-e0), Q(x-e1), Q(x-e2),
 //               Q(x-e0-e1) + p01, Q(x-e0-e2) + p02, Q(x-e1-e2) + p12,
 //               Q(x-e0-e1-e2) + p01 + p02 + p12 )
 // then m* = (W(x) - max) mod 8 and Q(x) = max + m*; m* is the traceback byte.
-// Traceback bytes are packed four positions per word and stored to the row-major
-// traceback tensor as aligned 32-bit words.
+// Each lane stores its R traceback bytes of a step as one 8-byte word into the
+// column-blocked traceback layout (see c3::tb_col_bytes), 256 contiguous bytes
+// per warp step.
 #include "api_internal.h"
 #include "device_common.cuh"
 
 namespace msadp {
 
 struct C3Smem {
-    int32_t ring[c3::W][c3::S][32];   // row -1 values of each warp, by lockstep step
-    int32_t f1[c3::S][c3::WR];        // axis-1 face of CTA (A, B-1)
-    int32_t corner0[c3::S][4];        // last row of CTA (A-1, B-1) at its last lane
+    int32_t ring0[c3::S][32];          // staged F0 of (A-1, B): row X at slot (X - 1) & (S - 1)
+    int32_t ringi[c3::W][c3::SI][32];  // warp w-1 -> warp w (index w >= 1), by lockstep step
+    int32_t f1[c3::S][c3::WR];         // staged F1 of (A, B-1): row X at slot X & (S - 1)
+    int32_t corner0[c3::S];            // F1 of (A-1, B-1), row X + WR - 1, entry WR - 1
+    int32_t staged;                    // chunks staged (written by the staging warp)
+    int32_t consumed;                  // chunks computed (written by compute thread 0)
+    int32_t failed;                    // a wait ran out: every warp leaves the column
+    int32_t go;                        // chunk-start decision of compute thread 0
     int32_t ctl[4];
     int32_t cur_prob;
 };
 
-int col3_warps_per_cta() { return c3::W; }
+int col3_warps_per_cta() { return c3::W + 1; }
 
-__device__ __forceinline__ void c3_cp16(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void c3_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void c3_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void c3_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-// byte-insert selectors: put the low byte of the second operand at byte b
-__device__ __forceinline__ constexpr unsigned c3_ins(int b) {
-    return b == 0 ? 0x3214u : b == 1 ? 0x3240u : b == 2 ? 0x3410u : 0x4210u;
+__device__ __forceinline__ int vload(const int32_t *p) { return *reinterpret_cast<const volatile int32_t *>(p); }
+__device__ __forceinline__ void vstore(int32_t *p, int v) { *reinterpret_cast<volatile int32_t *>(p) = v; }
+__device__ __forceinline__ void compute_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(c3::W * 32) : "memory"); }
+__device__ __forceinline__ int2 ld_relaxed_v2(const int32_t *p) {
+    int2 v;
+    asm volatile("ld.relaxed.gpu.global.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p) : "memory");
+    return v;
 }
 
 struct C3Col {
-    // column-constant state
     int A, B, nsteps, TS;
     int rho0, rho1, rho2, len2;
     const int32_t *f0src, *f1src, *c0src;  // producer faces (nullptr: none)
     int32_t *f0dst, *f1dst;                // this column's faces
-    int32_t *prog;                          // progress counters of this problem
-    int pA1, pB1, pAB1;                     // producer column indices (-1: none)
-    int me;
 };
 
-// Stage chunk c's faces into the shared rings (all threads; one commit group).
-__device__ __forceinline__ void c3_stage(C3Smem &sm, const C3Col &cc, int c, int tid) {
+// Staging warp: copy chunk c's face entries into the shared rings once every
+// needed entry carries this launch's tag. Entries outside the tensor (position
+// p < 0 or p >= rho2) are never needed and are staged as "no predecessor".
+// Returns false when the wait runs out or another warp gave up.
+__device__ bool c3_stage_chunk(C3Smem &sm, const C3Col &cc, int c, int lane, int epoch, const LaunchDesc &L) {
     const int T0 = c * c3::CH;
-    // F0 of (A-1, B): rows X in [T0, T0+CH) -> ring[0][(X-1) & (S-1)], 8 x 16 B per row
-    if (cc.f0src) {
-        for (int i = tid; i < c3::CH * 8; i += c3::THREADS) {
-            const int X = T0 + i / 8, part = i % 8;
-            c3_cp16(&sm.ring[0][(X - 1) & (c3::S - 1)][part * 4], cc.f0src + (int64_t)X * 32 + part * 4);
-        }
-    }
-    // F1 of (A, B-1): rows X in [T0, T0+CH) -> f1[X & (S-1)], 16 x 16 B per row
-    if (cc.f1src) {
-        for (int i = tid; i < c3::CH * 16; i += c3::THREADS) {
-            const int X = T0 + i / 16, part = i % 16;
-            c3_cp16(&sm.f1[X & (c3::S - 1)][part * 4], cc.f1src + (int64_t)X * c3::WR + part * 4);
-        }
-    }
-    // corner for warp 0 lane 0: F1 of (A-1, B-1) at row X + WR - 1, entries WR-4..WR-1
-    if (cc.c0src) {
-        for (int i = tid; i < c3::CH; i += c3::THREADS) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        int f0v[c3::CH], f1v[c3::CH][2], cv = kNeg;
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < c3::CH; ++i) {
             const int X = T0 + i;
-            c3_cp16(&sm.corner0[X & (c3::S - 1)][0],
-                    cc.c0src + (int64_t)(X + c3::WR - 1) * c3::WR + (c3::WR - 4));
+            // F0 entry (X, lane): position X - lane
+            int v = kNeg;
+            if (cc.f0src && (unsigned)(X - lane) < (unsigned)cc.rho2) {
+                const int2 e = ld_relaxed_v2(cc.f0src + (int64_t)X * c3::F0W + 2 * lane);
+                ok = ok && e.y == epoch;
+                v = e.x;
+            }
+            f0v[i] = v;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int rho = lane + 32 * h;  // F1 entry (X, rho): position X - rho
+                int u = kNeg;
+                if (cc.f1src && (unsigned)(X - rho) < (unsigned)cc.rho2) {
+                    const int2 e = ld_relaxed_v2(cc.f1src + (int64_t)X * c3::F1W + 2 * rho);
+                    ok = ok && e.y == epoch;
+                    u = e.x;
+                }
+                f1v[i][h] = u;
+            }
         }
+        if (lane < c3::CH) {  // corner: F1 of (A-1, B-1) row X + WR - 1, entry WR - 1: position X
+            const int X = T0 + lane;
+            if (cc.c0src && (unsigned)X < (unsigned)cc.rho2) {
+                const int2 e = ld_relaxed_v2(cc.c0src + (int64_t)(X + c3::WR - 1) * c3::F1W + 2 * (c3::WR - 1));
+                ok = ok && e.y == epoch;
+                cv = e.x;
+            }
+        }
+        if (__all_sync(kFull, ok)) {
+#pragma unroll
+            for (int i = 0; i < c3::CH; ++i) {
+                const int X = T0 + i;
+                sm.ring0[(X - 1) & (c3::S - 1)][lane] = f0v[i];
+                sm.f1[X & (c3::S - 1)][lane] = f1v[i][0];
+                sm.f1[X & (c3::S - 1)][lane + 32] = f1v[i][1];
+            }
+            if (lane < c3::CH) sm.corner0[(T0 + lane) & (c3::S - 1)] = cv;
+            return true;
+        }
+        if ((it & 7) == 7) {
+            if (vload(&sm.failed) || ld_volatile(L.err) != 0) return false;
+            if ((int64_t)(global_ns() - t0) > L.spin_ns) return false;
+        }
+        __nanosleep(128);
     }
-    c3_commit();
-}
-
-// Wait (thread 0) until the producers have completed the steps chunk c reads.
-__device__ __forceinline__ bool c3_wait_producers(const C3Col &cc, int c, const LaunchDesc &L) {
-    const int Xmax = c * c3::CH + c3::CH - 1;
-    bool ok = true;
-    if (cc.pA1 >= 0) ok = ok && wait_at_least(&cc.prog[cc.pA1], min(cc.nsteps, Xmax + c3::WR), L.err, L.spin_ns);
-    if (cc.pB1 >= 0) ok = ok && wait_at_least(&cc.prog[cc.pB1], min(cc.nsteps, Xmax + 32), L.err, L.spin_ns);
-    if (cc.pAB1 >= 0)
-        ok = ok && wait_at_least(&cc.prog[cc.pAB1], min(cc.nsteps, Xmax + c3::WR - 1 + 32), L.err, L.spin_ns);
-    return ok;
 }
 
 // Per-warp register state of one column.
 struct C3Regs {
-    int V[3][c3::R];      // own values by generation (step mod 3)
-    int U[3][c3::R];      // values received from lane l-1
-    int VM[3], UM[3];     // row -1 (warp above), own lane and lane l-1
-    int code[c3::R];      // axis-2 code of each row's current position
-    unsigned cur[c3::R];  // traceback bytes being packed (4 positions)
-    unsigned prv[c3::R];  // previous packed word
+    int V[3][c3::R];   // own values by generation (step mod 3)
+    int U[3][c3::R];   // values received from lane l-1
+    int VM[3], UM[3];  // row -1 (warp above), own lane and lane l-1
+    int code[c3::R];   // axis-2 code of each row's current position
+};
+
+// Column-constant inputs of a compute warp.
+struct C3Lane {
+    const int *tabr;          // replicated pair table
+    int rowoff[c3::R];        // byte offset of row r's table row (code of x0) in tabr
+    int laneoff;              // byte offset of this lane's table row (code of x1)
+    int p01[c3::R];           // scaled pair score of (x0, x1) per row
+    int Wb;                   // W(x) = Wb - 3 r + 4 t for row r at warp step t
+    const unsigned char *sc2; // axis-2 codes, indexed by position
+    const int32_t *vmring;    // row -1 source: staged face (warp 0) or the warp above
+    int vmask;
+    unsigned char *tbw;       // this lane's traceback bytes at warp step 0
+    int32_t *f0dst, *f1dst;
+    int lane, w, rho2, TS, tag;
+    bool origin;
 };
 
 template <bool MASK, int s>
-__device__ __forceinline__ void c3_step(C3Regs &g, C3Smem &sm, const int *__restrict__ tabr,
-                                        const int (&rowoff)[c3::R], int laneoff, const int (&p01)[c3::R],
-                                        const int (&Wc)[c3::R], const unsigned char *sc2, int T, int t,
-                                        int lane, int w, unsigned rowvalid, bool lanevalid, int rho2,
-                                        unsigned char *tbl, const int (&tbro)[c3::R], const unsigned (&selA)[4],
-                                        int32_t *f0dst, int32_t *f1dst, bool origin) {
+__device__ __forceinline__ void c3_step(C3Regs &g, C3Smem &sm, const C3Lane &c, int T, int t) {
     constexpr int cur = s % 3, prv = (s + 2) % 3, pv2 = (s + 1) % 3;
+    const int lane = c.lane, w = c.w;
     // receive lane l-1's values of the previous step; lane 0 takes the axis-1 face
     const int4 fa = *reinterpret_cast<const int4 *>(&sm.f1[T & (c3::S - 1)][w * c3::R]);
     const int4 fb = *reinterpret_cast<const int4 *>(&sm.f1[T & (c3::S - 1)][w * c3::R + 4]);
@@ -133,87 +164,79 @@ __device__ __forceinline__ void c3_step(C3Regs &g, C3Smem &sm, const int *__rest
         g.U[cur][r] = lane == 0 ? fl[r] : v;
     }
     // row -1 from the warp above (or the staged face of CTA (A-1, B))
-    g.VM[cur] = sm.ring[w][(T - 1) & (c3::S - 1)][lane];
+    g.VM[cur] = c.vmring[((T - 1) & c.vmask) * 32 + lane];
     {
-        const int um = sm.ring[w][(T - 2) & (c3::S - 1)][(lane + 31) & 31];
-        const int cw = w == 0 ? sm.corner0[T & (c3::S - 1)][3] : sm.f1[(T - 1) & (c3::S - 1)][w * c3::R - 1];
+        const int um = c.vmring[((T - 2) & c.vmask) * 32 + ((lane + 31) & 31)];
+        const int cw = w == 0 ? sm.corner0[T & (c3::S - 1)] : sm.f1[(T - 1) & (c3::S - 1)][w * c3::R - 1];
         g.UM[cur] = lane == 0 ? cw : um;
     }
     // shift the per-row axis-2 codes: row r now sits one position behind row r-1
 #pragma unroll
     for (int r = c3::R - 1; r > 0; --r) g.code[r] = g.code[r - 1];
-    g.code[0] = sc2[t - lane];
-    const int t4 = 4 * t;
+    g.code[0] = c.sc2[t - lane];
+    const int w4 = c.Wb + 4 * t;
     const int jl = t - lane;
+    int m8[c3::R];
 #pragma unroll
     for (int r = 0; r < c3::R; ++r) {
         const int c2 = g.code[r] << 7;  // table stride per code: 32 lanes * 4 bytes
-        const int p02 = *reinterpret_cast<const int *>(reinterpret_cast<const char *>(tabr) + rowoff[r] + c2);
-        const int p12 = *reinterpret_cast<const int *>(reinterpret_cast<const char *>(tabr) + laneoff + c2);
+        const char *tb = reinterpret_cast<const char *>(c.tabr);
+        const int p02 = *reinterpret_cast<const int *>(tb + c.rowoff[r] + c2);
+        const int p12 = *reinterpret_cast<const int *>(tb + c.laneoff + c2);
         const int v1m = r == 0 ? g.VM[cur] : g.V[prv][r - 1];
         const int v2m = r == 0 ? g.VM[prv] : g.V[pv2][r - 1];
         const int u1m = r == 0 ? g.UM[cur] : g.U[prv][r - 1];
         const int u2m = r == 0 ? g.UM[prv] : g.U[pv2][r - 1];
-        int acc = max(max(v1m, g.U[cur][r]), g.V[prv][r]);
-        acc = max(acc, u1m + p01[r]);
-        acc = max(acc, v2m + p02);
-        acc = max(acc, g.U[prv][r] + p12);
-        acc = max(acc, u2m + (p01[r] + p02 + p12));
+        // max over the seven moves, as a balanced tree
+        const int a = max(v1m, g.U[cur][r]);
+        const int b = max(g.V[prv][r], u1m + c.p01[r]);
+        const int d = max(v2m + p02, g.U[prv][r] + p12);
+        const int e = u2m + (c.p01[r] + p02 + p12);
+        const int acc = max(max(a, b), max(d, e));
         // strip the tie bits: Q = W + ceil8(acc - W), m* = Q - acc
-        const int wx = Wc[r] + t4;
+        const int wx = w4 - 3 * r;
         int q = ((acc - wx + 7) & ~7) + wx;
         int m = q - acc;
         if (MASK) {
-            const bool valid = (unsigned)(jl - r) < (unsigned)rho2;
+            const bool valid = (unsigned)(jl - r) < (unsigned)c.rho2;
             q = valid ? q : kNeg;
-            if (r == 0 && origin && jl == 0) {  // H(0) = 0, no move
+            if (r == 0 && c.origin && jl == 0) {  // H(0) = 0, no move
                 q = 0;
                 m = 0;
             }
         }
         g.V[cur][r] = q;
-        g.cur[r] = __byte_perm(g.cur[r], (unsigned)m, c3_ins(s & 3));
+        m8[r] = m;
+    }
+    // traceback bytes of the 8 rows: one 8-byte store per lane, 256 B per warp
+    {
+        const unsigned lo = (unsigned)m8[0] | (unsigned)m8[1] << 8 | (unsigned)m8[2] << 16 | (unsigned)m8[3] << 24;
+        const unsigned hi = (unsigned)m8[4] | (unsigned)m8[5] << 8 | (unsigned)m8[6] << 16 | (unsigned)m8[7] << 24;
+        *reinterpret_cast<uint2 *>(c.tbw + (int64_t)t * (c3::W * 32 * c3::R)) = make_uint2(lo, hi);
     }
     // faces: last row of the warp feeds the warp below; last lane feeds CTA (A, B+1)
     if (w + 1 < c3::W) {
-        sm.ring[w + 1][T & (c3::S - 1)][lane] = g.V[cur][c3::R - 1];
+        sm.ringi[w + 1][T & (c3::SI - 1)][lane] = g.V[cur][c3::R - 1];
     } else if (T - c3::WR + 1 >= 0) {
-        f0dst[(int64_t)(T - c3::WR + 1) * 32 + lane] = g.V[cur][c3::R - 1];
+        *reinterpret_cast<int2 *>(c.f0dst + (int64_t)(T - c3::WR + 1) * c3::F0W + 2 * lane) =
+            make_int2(g.V[cur][c3::R - 1], c.tag);
     }
     if (lane == 31 && T >= 31) {
-        int4 *d = reinterpret_cast<int4 *>(f1dst + (int64_t)(T - 31) * c3::WR + w * c3::R);
-        d[0] = make_int4(g.V[cur][0], g.V[cur][1], g.V[cur][2], g.V[cur][3]);
-        d[1] = make_int4(g.V[cur][4], g.V[cur][5], g.V[cur][6], g.V[cur][7]);
-    }
-    // every 4th step: store the aligned 4-position word of every row
-    if ((s & 3) == 3) {
-        const int base = jl - 3;  // positions [jl-r-3, jl-r] were packed in cur[r]
-#pragma unroll
-        for (int r = 0; r < c3::R; ++r) {
-            const unsigned word = __byte_perm(g.prv[r], g.cur[r], selA[r & 3]);
-            const int q0 = (base - r) & ~3;  // aligned start (see selA)
-            const bool ok = ((rowvalid >> r) & 1) && lanevalid && (!MASK || (q0 >= 0 && q0 < rho2));
-            if (ok) *reinterpret_cast<unsigned *>(tbl + tbro[r] + q0) = word;
-            g.prv[r] = g.cur[r];
-        }
+        int4 *d = reinterpret_cast<int4 *>(c.f1dst + (int64_t)(T - 31) * c3::F1W + 2 * w * c3::R);
+        d[0] = make_int4(g.V[cur][0], c.tag, g.V[cur][1], c.tag);
+        d[1] = make_int4(g.V[cur][2], c.tag, g.V[cur][3], c.tag);
+        d[2] = make_int4(g.V[cur][4], c.tag, g.V[cur][5], c.tag);
+        d[3] = make_int4(g.V[cur][6], c.tag, g.V[cur][7], c.tag);
     }
 }
 
 template <bool MASK>
-__device__ __forceinline__ void c3_chunk(C3Regs &g, C3Smem &sm, const int *__restrict__ tabr,
-                                         const int (&rowoff)[c3::R], int laneoff, const int (&p01)[c3::R],
-                                         const int (&Wc)[c3::R], const unsigned char *sc2, int T0, int lane,
-                                         int w, unsigned rowvalid, bool lanevalid, int rho2, int TS,
-                                         unsigned char *tbl, const int (&tbro)[c3::R],
-                                         const unsigned (&selA)[4], int32_t *f0dst, int32_t *f1dst,
-                                         bool origin) {
-#define C3_STEP(s)                                                                                        \
-    {                                                                                                     \
-        const int T = T0 + (s), t = T - w * c3::R;                                                        \
-        if (t >= 0 && t < TS)                                                                             \
-            c3_step<MASK, (s)>(g, sm, tabr, rowoff, laneoff, p01, Wc, sc2, T, t, lane, w, rowvalid,        \
-                               lanevalid, rho2, tbl, tbro, selA, f0dst, f1dst, origin);                    \
-        __syncthreads();                                                                                  \
+__device__ __forceinline__ void c3_chunk(C3Regs &g, C3Smem &sm, const C3Lane &c, int T0) {
+#define C3_STEP(s)                                            \
+    {                                                         \
+        const int T = T0 + (s), t = T - c.w * c3::R;          \
+        if (t >= 0 && t < c.TS) c3_step<MASK, (s)>(g, sm, c, T, t); \
+        compute_barrier();                                    \
     }
     C3_STEP(0) C3_STEP(1) C3_STEP(2) C3_STEP(3) C3_STEP(4) C3_STEP(5)
     C3_STEP(6) C3_STEP(7) C3_STEP(8) C3_STEP(9) C3_STEP(10) C3_STEP(11)
@@ -227,6 +250,7 @@ __global__ void __launch_bounds__(c3::THREADS, 1) fill_col3_kernel(const LaunchD
     unsigned char *sc2base = reinterpret_cast<unsigned char *>(tabr + L.tab_ints);  // axis-2 codes
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const bool stager = w == c3::W;
     if (tid == 0) sm.cur_prob = -1;
     __syncthreads();
 
@@ -244,12 +268,12 @@ __global__ void __launch_bounds__(c3::THREADS, 1) fill_col3_kernel(const LaunchD
         const uint64_t ent = L.order[ticket];
         const int pidx = (int)(ent >> 32);
         const ProblemDesc &P = L.probs[pidx];
+        if (ld_volatile(&P.istat->status) != 0) continue;  // uniform: every thread reads the same word
         const int lin = (int)(uint32_t)ent;
         const int NB = P.G[1];
         C3Col cc;
         cc.A = lin / NB;
         cc.B = lin - cc.A * NB;
-        cc.me = lin;
         cc.rho0 = P.rho[0];
         cc.rho1 = P.rho[1];
         cc.rho2 = P.rho[2];
@@ -257,67 +281,91 @@ __global__ void __launch_bounds__(c3::THREADS, 1) fill_col3_kernel(const LaunchD
         cc.TS = cc.rho2 + c3::R + 31 + c3::EXTRA;
         cc.nsteps = c3::nsteps(cc.rho2);
         const int nchunks = cc.nsteps / c3::CH;
-        cc.prog = L.done + P.tile_base;
-        const int32_t *F0 = P.Q;
-        const int32_t *F1 = P.aux;
         cc.f0dst = P.Q + (int64_t)lin * P.face0_stride;
         cc.f1dst = P.aux + (int64_t)lin * P.face1_stride;
-        cc.pA1 = cc.A > 0 ? lin - NB : -1;
-        cc.pB1 = cc.B > 0 ? lin - 1 : -1;
-        cc.pAB1 = (cc.A > 0 && cc.B > 0) ? lin - NB - 1 : -1;
-        cc.f0src = cc.pA1 >= 0 ? F0 + (int64_t)cc.pA1 * P.face0_stride : nullptr;
-        cc.f1src = cc.pB1 >= 0 ? F1 + (int64_t)cc.pB1 * P.face1_stride : nullptr;
-        cc.c0src = cc.pAB1 >= 0 ? F1 + (int64_t)cc.pAB1 * P.face1_stride : nullptr;
-        const bool live = ld_volatile(&P.istat->status) == 0;
+        cc.f0src = cc.A > 0 ? P.Q + (int64_t)(lin - NB) * P.face0_stride : nullptr;
+        cc.f1src = cc.B > 0 ? P.aux + (int64_t)(lin - 1) * P.face1_stride : nullptr;
+        cc.c0src = (cc.A > 0 && cc.B > 0) ? P.aux + (int64_t)(lin - NB - 1) * P.face1_stride : nullptr;
+        // a withheld column (test hook) writes faces no reader accepts
+        const int tag = (int64_t)ticket == L.withhold ? 0 : L.epoch;
 
-        if (live) {
-            const int A = P.A;
-            // replicated pair table (entry-major, one copy per lane) and axis-2 codes
-            const int have = sm.cur_prob;
-            __syncthreads();
-            if (have != pidx)
-                for (int i = tid; i < A * A * 32; i += c3::THREADS) tabr[i] = P.tab[i >> 5];
-            if (tid == 0) sm.cur_prob = pidx;
-            for (int i = tid; i < cc.rho2 + 2 * c3::CODEPAD + 32; i += c3::THREADS) {
-                const int j = i - c3::CODEPAD;  // position x2 = j consumes residue j - 1
-                sc2base[i] = (j >= 1 && j <= cc.len2) ? P.codes[P.cofs[2] + j - 1] : (unsigned char)0;
+        const int A = P.A;
+        // replicated pair table (entry-major, one copy per lane) and axis-2 codes
+        const int have = sm.cur_prob;
+        __syncthreads();
+        if (have != pidx)
+            for (int i = tid; i < A * A * 32; i += c3::THREADS) tabr[i] = P.tab[i >> 5];
+        if (tid == 0) {
+            sm.cur_prob = pidx;
+            sm.staged = 0;
+            sm.consumed = 0;
+            sm.failed = 0;
+        }
+        for (int i = tid; i < cc.rho2 + 2 * c3::CODEPAD + 32; i += c3::THREADS) {
+            const int j = i - c3::CODEPAD;  // position x2 = j consumes residue j - 1
+            sc2base[i] = (j >= 1 && j <= cc.len2) ? P.codes[P.cofs[2] + j - 1] : (unsigned char)0;
+        }
+        // rings start at "no predecessor"
+        for (int i = tid; i < c3::S * 32; i += c3::THREADS) (&sm.ring0[0][0])[i] = kNeg;
+        for (int i = tid; i < c3::W * c3::SI * 32; i += c3::THREADS) (&sm.ringi[0][0][0])[i] = kNeg;
+        for (int i = tid; i < c3::S * c3::WR; i += c3::THREADS) (&sm.f1[0][0])[i] = kNeg;
+        for (int i = tid; i < c3::S; i += c3::THREADS) sm.corner0[i] = kNeg;
+        __syncthreads();
+
+        if (stager) {
+            for (int c = 0; c < nchunks; ++c) {
+                // back-pressure: at most AHEAD chunks beyond the compute warps
+                const uint64_t t0 = global_ns();
+                bool ok = true;
+                while (vload(&sm.consumed) <= c - c3::AHEAD) {
+                    if (vload(&sm.failed) || ld_volatile(L.err) != 0 ||
+                        (int64_t)(global_ns() - t0) > L.spin_ns) {
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                ok = ok && c3_stage_chunk(sm, cc, c, lane, L.epoch, L);
+                if (!ok) {
+                    if (lane == 0) {
+                        vstore(&sm.failed, 1);
+                        atomicCAS(L.err, 0, MSA_ETIMEOUT);
+                    }
+                    break;
+                }
+                __syncwarp();
+                __threadfence_block();
+                if (lane == 0) vstore(&sm.staged, c + 1);
             }
-            // rings start at "no predecessor"
-            for (int i = tid; i < c3::W * c3::S * 32; i += c3::THREADS) (&sm.ring[0][0][0])[i] = kNeg;
-            for (int i = tid; i < c3::S * c3::WR; i += c3::THREADS) (&sm.f1[0][0])[i] = kNeg;
-            for (int i = tid; i < c3::S * 4; i += c3::THREADS) (&sm.corner0[0][0])[i] = kNeg;
-            __syncthreads();
-
+        } else {
             // column constants of this lane
+            C3Lane cl;
+            cl.lane = lane;
+            cl.w = w;
+            cl.rho2 = cc.rho2;
+            cl.TS = cc.TS;
+            cl.tag = tag;
+            cl.tabr = tabr;
+            cl.f0dst = cc.f0dst;
+            cl.f1dst = cc.f1dst;
             const int x1 = cc.B * 32 + lane;
-            const bool lanevalid = x1 < cc.rho1;
             const int code1 = (x1 >= 1 && x1 <= P.len[1]) ? P.codes[P.cofs[1] + x1 - 1] : 0;
             const int x0b = cc.A * c3::WR + w * c3::R;
-            int rowoff[c3::R], p01[c3::R], Wc[c3::R], tbro[c3::R];
-            unsigned rowvalid = 0;
 #pragma unroll
             for (int r = 0; r < c3::R; ++r) {
                 const int x0 = x0b + r;
                 const int code0 = (x0 >= 1 && x0 <= P.len[0]) ? P.codes[P.cofs[0] + x0 - 1] : 0;
-                rowoff[r] = (code0 * A * 32 + lane) * 4;
-                p01[r] = P.tab[code0 * A + code1];
-                // W(x) = x0 + 2 x1 + 4 x2 with x2 = t - lane - r
-                Wc[r] = x0 + 2 * x1 - 4 * lane - 4 * r;
-                if (x0 < cc.rho0) rowvalid |= 1u << r;
-                tbro[r] = (int)((int64_t)r * P.tbstride[0]);
+                cl.rowoff[r] = (code0 * A * 32 + lane) * 4;
+                cl.p01[r] = P.tab[code0 * A + code1];
             }
-            const int laneoff = (code1 * A * 32 + lane) * 4;
-            unsigned char *tbl = P.tb + (int64_t)min(x0b, cc.rho0 - 1) * P.tbstride[0] +
-                                 (int64_t)min(x1, cc.rho1 - 1) * P.tbstride[1];
-            if (x0b >= cc.rho0) rowvalid = 0;
-            // byte selectors aligning a packed word with the 4-aligned positions:
-            // row r's word ends at j = t - lane - r with (j - 3) = -(lane + r) mod 4
-            unsigned selA[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int o = 4 - ((-(lane + k)) & 3);
-                selA[k] = (unsigned)(o | (o + 1) << 4 | (o + 2) << 8 | (o + 3) << 12);
-            }
+            cl.laneoff = (code1 * A * 32 + lane) * 4;
+            // W(x) = x0 + 2 x1 + 4 x2 with x0 = x0b + r, x2 = t - lane - r
+            cl.Wb = x0b + 2 * x1 - 4 * lane;
+            cl.tbw = P.tb + (int64_t)lin * c3::tb_col_bytes(cc.rho2) + (int64_t)(w * 32 + lane) * c3::R;
+            cl.vmring = w == 0 ? &sm.ring0[0][0] : &sm.ringi[w][0][0];
+            cl.vmask = w == 0 ? c3::S - 1 : c3::SI - 1;
+            cl.sc2 = sc2base + c3::CODEPAD;
+            cl.origin = cc.A == 0 && cc.B == 0 && w == 0 && lane == 0;
 
             C3Regs g;
 #pragma unroll
@@ -328,66 +376,46 @@ __global__ void __launch_bounds__(c3::THREADS, 1) fill_col3_kernel(const LaunchD
                     g.U[k][r] = kNeg;
                 }
                 g.code[r] = 0;
-                g.cur[r] = 0;
-                g.prv[r] = 0;
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 g.VM[k] = kNeg;
                 g.UM[k] = kNeg;
             }
-            const unsigned char *sc2 = sc2base + c3::CODEPAD;
-            const bool origin = cc.A == 0 && cc.B == 0 && w == 0 && lane == 0;
 
-            // prologue: stage chunk 0
-            if (tid == 0) sm.ctl[2] = c3_wait_producers(cc, 0, L) ? 0 : 1;
-            __syncthreads();
-            bool failed = sm.ctl[2] != 0;
-            if (!failed) c3_stage(sm, cc, 0, tid);
-            for (int c = 0; c < nchunks && !failed; ++c) {
-                // prefetch chunk c+1 while chunk c computes
-                if (c + 1 < nchunks) {
-                    if (tid == 0) sm.ctl[2] = c3_wait_producers(cc, c + 1, L) ? 0 : 1;
-                    __syncthreads();
-                    if (sm.ctl[2] != 0) {
-                        failed = true;
-                        break;
+            for (int c = 0; c < nchunks; ++c) {
+                if (tid == 0) {
+                    const uint64_t t0 = global_ns();
+                    int go = 1;
+                    while (vload(&sm.staged) <= c) {
+                        if (vload(&sm.failed) || (int64_t)(global_ns() - t0) > L.spin_ns) {
+                            go = 0;
+                            break;
+                        }
+                        __nanosleep(32);
                     }
-                    c3_stage(sm, cc, c + 1, tid);
-                    c3_wait_prev();
-                } else {
-                    c3_wait_all();
+                    if (!go) {
+                        vstore(&sm.failed, 1);
+                        atomicCAS(L.err, 0, MSA_ETIMEOUT);
+                    }
+                    sm.go = go;
                 }
-                __syncthreads();
+                compute_barrier();
+                if (!sm.go) break;
+                __threadfence_block();
                 const int T0 = c * c3::CH;
                 const int t0 = T0 - w * c3::R;
-                // interior chunk for this warp: every (lane, row) position inside [4, rho2)
-                const bool interior = t0 - 31 - (c3::R - 1) >= 7 && t0 + c3::CH - 1 <= cc.rho2 - 1;
+                // interior chunk for this warp: every (lane, row) position inside [1, rho2)
+                const bool interior = t0 - 31 - (c3::R - 1) >= 1 && t0 + c3::CH - 1 <= cc.rho2 - 1;
                 if (interior)
-                    c3_chunk<false>(g, sm, tabr, rowoff, laneoff, p01, Wc, sc2, T0, lane, w, rowvalid, lanevalid,
-                                    cc.rho2, cc.TS, tbl, tbro, selA, cc.f0dst, cc.f1dst, origin);
+                    c3_chunk<false>(g, sm, cl, T0);
                 else
-                    c3_chunk<true>(g, sm, tabr, rowoff, laneoff, p01, Wc, sc2, T0, lane, w, rowvalid, lanevalid,
-                                   cc.rho2, cc.TS, tbl, tbro, selA, cc.f0dst, cc.f1dst, origin);
-                // publish progress (all steps of the chunk are done: the last step ended in a barrier)
-                if (tid == 0 && (int64_t)ticket != L.withhold) {
-                    __threadfence();
-                    st_release(&cc.prog[cc.me], T0 + c3::CH);
-                }
-            }
-            c3_wait_all();
-            __syncthreads();
-            if (failed) {
-                if (tid == 0) atomicCAS(L.err, 0, MSA_ETIMEOUT);
-                break;
-            }
-        } else {
-            if (tid == 0 && (int64_t)ticket != L.withhold) {
-                __threadfence();
-                st_release(&cc.prog[cc.me], cc.nsteps);
+                    c3_chunk<true>(g, sm, cl, T0);
+                if (tid == 0) vstore(&sm.consumed, c + 1);
             }
         }
         __syncthreads();
+        if (vload(&sm.failed)) break;
     }
 }
 

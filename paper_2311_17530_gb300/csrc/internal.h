@@ -49,6 +49,8 @@ struct ProblemDesc {
     int64_t face1_stride;        // column kernel: ints per column in aux (axis-1 faces)
     int32_t face0_rows;          // column kernel: skewed rows per axis-0 face
     int32_t face1_rows;          // column kernel: skewed rows per axis-1 face
+    int32_t tb_layout;           // 0: row-major (tbstride); 1: column-blocked (column kernel)
+    int32_t pad3;
     const uint8_t *amap;         // device 256-entry char -> code map (0xFF: invalid)
     uint8_t *codes;              // device codes
     int32_t *tab;                // device scaled pair table ((sub - 2 gap) << B)
@@ -82,6 +84,8 @@ struct LaunchDesc {
     int64_t withhold;        // test hook: this ticket never publishes (-1: off)
     int32_t nprob;
     int32_t tab_ints;        // column kernel: shared-memory ints of the replicated table
+    int32_t epoch;           // column kernel: tag of this launch's face entries (>= 1)
+    int32_t pad2;
 };
 
 // Tile extents of the generic kernel, per k (compile-time in the kernel).
@@ -97,14 +101,16 @@ __host__ __device__ constexpr int tile_extent(int k, int i) {
 // k = 3 column kernel geometry (shared by the planner and the kernel).
 namespace c3 {
 constexpr int R = 8;         // rows per warp along axis 0 (registers)
-constexpr int W = 8;         // warps per CTA, stacked along axis 0
+constexpr int W = 8;         // compute warps per CTA, stacked along axis 0
 constexpr int WR = R * W;    // rows per CTA
-constexpr int CH = 12;       // lockstep steps per chunk (staging + progress granularity)
-constexpr int S = 32;        // shared ring slots
-constexpr int THREADS = 32 * W;
+constexpr int CH = 12;       // lockstep steps per chunk (staging granularity)
+constexpr int S = 64;        // slots of the staged face rings (global inputs)
+constexpr int SI = 4;        // slots of the rings between compute warps
+constexpr int AHEAD = 4;     // chunks the staging warp may run ahead
+constexpr int THREADS = 32 * (W + 1);  // compute warps + one staging warp
 constexpr int MAXA = 24;     // largest alphabet (replicated pair table)
 constexpr int MAXRHO2 = 4096;  // largest axis-2 extent (staged codes)
-constexpr int EXTRA = 8;     // sweep steps past the last position (flushes packed words)
+constexpr int EXTRA = 0;     // sweep steps past the last position
 constexpr int CODEPAD = 64;  // axis-2 code staging pad on both sides
 // lockstep steps of one column: sweep TS = rho2 + R + 31 + EXTRA per warp, warps
 // lagging R steps each, rounded up to whole chunks
@@ -113,6 +119,16 @@ __host__ __device__ constexpr int nsteps(int rho2) {
 }
 __host__ __device__ constexpr int face0_rows(int rho2) { return nsteps(rho2) + CH; }
 __host__ __device__ constexpr int face1_rows(int rho2) { return nsteps(rho2) + WR + CH; }
+// Traceback bytes of the column kernel are stored column-blocked and skewed:
+// column (A, B) owns sweep(rho2) * W * 32 * R bytes, and the move of cell
+// (x0 = A*WR + w*R + r, x1 = 32B + l, x2) sits at ((t*W + w)*32 + l)*R + r with
+// t = x2 + l + r, the warp step that computes it; so each warp step stores one
+// contiguous run of 32 lanes x R bytes.
+__host__ __device__ constexpr int sweep(int rho2) { return rho2 + R + 31 + EXTRA; }
+__host__ __device__ constexpr int64_t tb_col_bytes(int rho2) { return (int64_t)sweep(rho2) * W * 32 * R; }
+// faces hold (value, epoch tag) pairs: 2 ints per entry
+constexpr int F0W = 32 * 2;  // ints per axis-0 face row
+constexpr int F1W = WR * 2;  // ints per axis-1 face row
 }  // namespace c3
 
 // Traceback box edge D per k (the box [x-D, x] is staged in shared memory; rows

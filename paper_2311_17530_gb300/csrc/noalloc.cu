@@ -115,6 +115,7 @@ int noalloc_plan(int k, const int32_t *lens, int A, HostPlan &hp) {
         s *= (i == k - 1) ? (hp.rho[i] + kTbRowAlign - 1) / kTbRowAlign * kTbRowAlign : hp.rho[i];
     }
     hp.tbbytes = s;
+    hp.tb_dev_bytes = s;
     return MSA_OK;
 }
 

@@ -126,22 +126,26 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
         s *= (i == k - 1) ? round_up64(hp.rho[i], kTbRowAlign) : hp.rho[i];
     }
     hp.tbbytes = s;
+    hp.tb_layout = 0;
+    hp.tb_dev_bytes = hp.tbbytes;
 
     if (hp.kernel == kKernelCol3) {
         // faces between columns and the column order: a column (a, b) can start
-        // about a*(WR + 2 CH) + b*(32 + 2 CH) lockstep steps after the first, so
+        // about a*(WR + CH) + b*(32 + CH) lockstep steps after the first, so
         // tickets follow that estimate (every producer gets a smaller ticket)
         const int rho2 = hp.rho[2];
         hp.face0_rows = c3::face0_rows(rho2);
         hp.face1_rows = c3::face1_rows(rho2);
-        hp.face0_stride = (int64_t)hp.face0_rows * 32;
-        hp.face1_stride = (int64_t)hp.face1_rows * c3::WR;
+        hp.face0_stride = (int64_t)hp.face0_rows * c3::F0W;
+        hp.face1_stride = (int64_t)hp.face1_rows * c3::F1W;
         hp.qelems = nt * hp.face0_stride;
         hp.aux_elems = nt * hp.face1_stride;
+        hp.tb_layout = 1;
+        hp.tb_dev_bytes = nt * c3::tb_col_bytes(rho2);
         std::vector<std::pair<int64_t, int64_t>> key(nt);
         for (int64_t t = 0; t < nt; ++t) {
             const int64_t a = t / hp.G[1], b = t % hp.G[1];
-            key[t] = {a * (c3::WR + 2 * c3::CH) + b * (32 + 2 * c3::CH), t};
+            key[t] = {a * (c3::WR + c3::CH) + b * (32 + c3::CH), t};
         }
         std::sort(key.begin(), key.end());
         hp.order.resize(nt);

@@ -31,8 +31,10 @@ struct HostPlan {
     int64_t face1_stride = 0;
     int32_t face0_rows = 0;
     int32_t face1_rows = 0;
-    int64_t tbstride[MSA_MAX_K] = {};
-    int64_t tbbytes = 0;
+    int64_t tbstride[MSA_MAX_K] = {};  // row-major strides (the layout msa_plan_read_tb returns)
+    int64_t tbbytes = 0;               // row-major size
+    int32_t tb_layout = 0;             // device layout: 0 row-major, 1 column-blocked
+    int64_t tb_dev_bytes = 0;          // device size of the traceback tensor
     int32_t pair_min_sum = 0;
     int32_t w_corner = 0;
     int32_t len_sum = 0;
