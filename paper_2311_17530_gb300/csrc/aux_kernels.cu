@@ -90,9 +90,13 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // column (A, B) as long as it can; the warp stages a window of that column --
 // lockstep steps [t - 24, t + 7], every warp block w, lanes [l0, l0 + 16) -- as
 // 8 x 16-byte runs per (step, w), and lane 0 walks inside it.
-constexpr int kTbcSteps = 32;   // steps per window
-constexpr int kTbcLanes = 16;   // lanes per window
-constexpr int kTbcBytes = kTbcSteps * c3::W * kTbcLanes * c3::R;  // 32 KB
+constexpr int kTbcSteps = 32;                          // steps per window
+constexpr int kTbcLanes = 16;                          // lanes per window
+constexpr int kTbcRow = kTbcLanes * c3::R;             // bytes per (step, warp block) in a window
+constexpr int kTbcParts = kTbcRow / 16;                // 16-byte copies per (step, warp block)
+constexpr int kTbcAlign = 16 / c3::R;                  // window start lane: 16-byte aligned
+constexpr int kTbcBytes = kTbcSteps * c3::W * kTbcRow;
+static_assert(kTbcBytes <= kTracebackSmem, "traceback window exceeds its shared memory");
 
 __device__ void traceback_col3(const ProblemDesc &P, const IODesc &io, unsigned char *box, int lane) {
     const int nsym = P.A, bits = P.B;  // alphabet size, tie bits
@@ -107,14 +111,14 @@ __device__ void traceback_col3(const ProblemDesc &P, const IODesc &io, unsigned 
         const int l = x1 & 31, r = x0 & (c3::R - 1);
         const int t = x2 + l + r;
         const int t_lo = t - (kTbcSteps - 8);
-        const int l0 = max(0, l - (kTbcLanes - 2)) & ~1;  // even, and l0 <= l < l0 + 16
+        const int l0 = max(0, l - (kTbcLanes - kTbcAlign)) & ~(kTbcAlign - 1);  // l0 <= l < l0 + 16
         const unsigned char *col = P.tb + (int64_t)(cA * NB + cB) * colb;
         // rows of the window: (step, w) pairs, 8 x 16 B each
-        for (int i = lane; i < kTbcSteps * c3::W * 8; i += 32) {
-            const int part = i & 7, row = i >> 3;
+        for (int i = lane; i < kTbcSteps * c3::W * kTbcParts; i += 32) {
+            const int part = i % kTbcParts, row = i / kTbcParts;
             const int tt = t_lo + row / c3::W, w = row % c3::W;
             if (tt >= 0 && tt < c3::sweep(rho2))
-                cp_async_16(box + row * (kTbcLanes * c3::R) + part * 16,
+                cp_async_16(box + row * kTbcRow + part * 16,
                             col + ((int64_t)(tt * c3::W + w) * 32 + l0) * c3::R + part * 16);
         }
         cp_async_wait_all();
@@ -123,11 +127,11 @@ __device__ void traceback_col3(const ProblemDesc &P, const IODesc &io, unsigned 
             const int before = ncols;
             while ((x0 | x1 | x2) != 0) {
                 const int ca = x0 / c3::WR, cb = x1 >> 5;
-                const int ll = x1 & 31, rr = x0 & (c3::R - 1), ww = (x0 % c3::WR) >> 3;
+                const int ll = x1 & 31, rr = x0 & (c3::R - 1), ww = (x0 % c3::WR) / c3::R;
                 const int tt = x2 + ll + rr;
                 if (ca != cA || cb != cB || ll < l0 || ll >= l0 + kTbcLanes || tt < t_lo || tt >= t_lo + kTbcSteps)
                     break;
-                const int m = box[((tt - t_lo) * c3::W + ww) * (kTbcLanes * c3::R) + (ll - l0) * c3::R + rr];
+                const int m = box[((tt - t_lo) * c3::W + ww) * kTbcRow + (ll - l0) * c3::R + rr];
                 if (m == 0 || m > 7 || ((m & 1) && x0 == 0) || ((m & 2) && x1 == 0) || ((m & 4) && x2 == 0) ||
                     ncols >= P.len_sum) {
                     fail = 1;

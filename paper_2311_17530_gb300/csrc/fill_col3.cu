@@ -74,7 +74,8 @@ __device__ bool c3_stage_chunk(C3Smem &sm, const C3Col &cc, int c, int lane, int
     const int T0 = c * c3::CH;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0;; ++it) {
-        int f0v[c3::CH], f1v[c3::CH][2], cv = kNeg;
+        constexpr int H = (c3::WR + 31) / 32;  // F1 entries per lane and row
+        int f0v[c3::CH], f1v[c3::CH][H], cv = kNeg;
         bool ok = true;
 #pragma unroll
         for (int i = 0; i < c3::CH; ++i) {
@@ -88,10 +89,10 @@ __device__ bool c3_stage_chunk(C3Smem &sm, const C3Col &cc, int c, int lane, int
             }
             f0v[i] = v;
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < H; ++h) {
                 const int rho = lane + 32 * h;  // F1 entry (X, rho): position X - rho
                 int u = kNeg;
-                if (cc.f1src && (unsigned)(X - rho) < (unsigned)cc.rho2) {
+                if (cc.f1src && rho < c3::WR && (unsigned)(X - rho) < (unsigned)cc.rho2) {
                     const int2 e = ld_relaxed_v2(cc.f1src + (int64_t)X * c3::F1W + 2 * rho);
                     ok = ok && e.y == epoch;
                     u = e.x;
@@ -112,8 +113,9 @@ __device__ bool c3_stage_chunk(C3Smem &sm, const C3Col &cc, int c, int lane, int
             for (int i = 0; i < c3::CH; ++i) {
                 const int X = T0 + i;
                 sm.ring0[(X - 1) & (c3::S - 1)][lane] = f0v[i];
-                sm.f1[X & (c3::S - 1)][lane] = f1v[i][0];
-                sm.f1[X & (c3::S - 1)][lane + 32] = f1v[i][1];
+#pragma unroll
+                for (int h = 0; h < H; ++h)
+                    if (lane + 32 * h < c3::WR) sm.f1[X & (c3::S - 1)][lane + 32 * h] = f1v[i][h];
             }
             if (lane < c3::CH) sm.corner0[(T0 + lane) & (c3::S - 1)] = cv;
             return true;

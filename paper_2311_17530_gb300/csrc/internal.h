@@ -101,7 +101,7 @@ __host__ __device__ constexpr int tile_extent(int k, int i) {
 // k = 3 column kernel geometry (shared by the planner and the kernel).
 namespace c3 {
 constexpr int R = 8;         // rows per warp along axis 0 (registers)
-constexpr int W = 8;         // compute warps per CTA, stacked along axis 0
+constexpr int W = 4;         // compute warps per CTA, stacked along axis 0 (one per SM sub-partition)
 constexpr int WR = R * W;    // rows per CTA
 constexpr int CH = 12;       // lockstep steps per chunk (staging granularity)
 constexpr int S = 64;        // slots of the staged face rings (global inputs)
