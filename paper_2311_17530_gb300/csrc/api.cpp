@@ -370,9 +370,9 @@ int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_su
     L.spin_ns = spin_ms * 1000000LL;
     L.withhold = withhold;
     L.nprob = 1;
-    L.tab_ints = plan->hp.A * plan->hp.A * 32;
+    L.tab_ints = plan->hp.A * (plan->hp.A + 1) * 32;  // table plus the sentinel column
     if (plan->hp.kernel == kKernelCol3) {
-        if (plan->epoch >= (1 << 30)) {  // tags would wrap: start over from cleared faces
+        if (plan->epoch >= 32767) {  // tags (epoch << 16) + T would wrap: start over from cleared faces
             e = clear_faces(plan->hp, plan->pp, s);
             if (e != cudaSuccess) return cuda_error(e, "face reset");
             plan->epoch = 0;
@@ -432,7 +432,7 @@ int msa_plan_read_tb(msa_plan *plan, void *host_dst, int64_t bytes) {
     const int rho2 = hp.rho[2];
     const int64_t colb = c3::tb_col_bytes(rho2);
     for (int x0 = 0; x0 < hp.rho[0]; ++x0) {
-        const int A = x0 / c3::WR, w = (x0 % c3::WR) / c3::R, r = x0 % c3::R;
+        const int A = x0 / c3::WR, rho = x0 % c3::WR, w = rho / c3::R, r = rho % c3::R;
         for (int x1 = 0; x1 < hp.rho[1]; ++x1) {
             const int B = x1 / 32, l = x1 % 32;
             const uint8_t *col = dev.data() + (int64_t)(A * hp.G[1] + B) * colb;
@@ -440,8 +440,8 @@ int msa_plan_read_tb(msa_plan *plan, void *host_dst, int64_t bytes) {
             for (int x2 = 0; x2 < rho2; ++x2) {
                 const int64_t dst = base + x2;
                 if (dst >= bytes) continue;
-                const int t = x2 + l + r;
-                out[dst] = col[((int64_t)(t * c3::W + w) * 32 + l) * c3::R + r];
+                const int T = x2 + l + rho;  // CTA time of the cell
+                out[dst] = col[((int64_t)((T + c3::U) * c3::W + w) * 32 + l) * c3::R + r];
             }
         }
     }

@@ -49,9 +49,12 @@ __global__ void encode_kernel(const ProblemDesc *probs, const IODesc *io_arr, IO
         if (sbad & 1) atomicCAS(&st->status, 0, MSA_EINVAL);
         // |H'| <= maxp * sum_{i<j} min(len_i, len_j); a candidate adds at most
         // C(k,2) * maxp; keys carry the factor 2^B and the potential W <= W(len).
+        // The margin 4 * (len_sum + 64) keeps the k = 3 column kernel's skew cells
+        // (x2 < 0, seeded at kNeg, tie bits adding at most 7 per cell along a path
+        // of at most len_sum + 63 cells) strictly below every valid key.
         const int64_t npairs = (int64_t)P.k * (P.k - 1) / 2;
-        const int64_t key_bound =
-            (int64_t)smax * (P.pair_min_sum + npairs) * ((int64_t)1 << B) + P.w_corner;
+        const int64_t key_bound = (int64_t)smax * (P.pair_min_sum + npairs) * ((int64_t)1 << B) + P.w_corner +
+                                  4 * ((int64_t)P.len_sum + 64);
         const int64_t g = io.gap < 0 ? -(int64_t)io.gap : (int64_t)io.gap;
         const int64_t score_bound = (int64_t)smax * P.pair_min_sum + g * (P.k - 1) * P.len_sum;
         if ((sbad & 2) || key_bound >= kKeyLimit || score_bound >= ((int64_t)1 << 31) - 1)
@@ -88,8 +91,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Traceback over the k = 3 column kernel's layout. The walk stays inside one
 // column (A, B) as long as it can; the warp stages a window of that column --
-// lockstep steps [t - 24, t + 7], every warp block w, lanes [l0, l0 + 16) -- as
-// 8 x 16-byte runs per (step, w), and lane 0 walks inside it.
+// CTA times [T - 24, T + 7], every warp block w, lanes [l0, l0 + 16) -- as
+// 16-byte runs per (time, w), and lane 0 walks inside it. Every move lowers the
+// CTA time T = x2 + l + (x0 mod WR) of the walk by its number of moved sequences.
 constexpr int kTbcSteps = 32;                          // steps per window
 constexpr int kTbcLanes = 16;                          // lanes per window
 constexpr int kTbcRow = kTbcLanes * c3::R;             // bytes per (step, warp block) in a window
@@ -108,18 +112,17 @@ __device__ void traceback_col3(const ProblemDesc &P, const IODesc &io, unsigned 
     int score = 0, ncols = 0, fail = 0;
     while ((x0 | x1 | x2) != 0 && !fail) {
         const int cA = x0 / c3::WR, cB = x1 >> 5;
-        const int l = x1 & 31, r = x0 & (c3::R - 1);
-        const int t = x2 + l + r;
-        const int t_lo = t - (kTbcSteps - 8);
+        const int l = x1 & 31;
+        const int t_lo = x2 + l + x0 % c3::WR - (kTbcSteps - 8);
         const int l0 = max(0, l - (kTbcLanes - kTbcAlign)) & ~(kTbcAlign - 1);  // l0 <= l < l0 + 16
         const unsigned char *col = P.tb + (int64_t)(cA * NB + cB) * colb;
         // rows of the window: (step, w) pairs, 8 x 16 B each
         for (int i = lane; i < kTbcSteps * c3::W * kTbcParts; i += 32) {
             const int part = i % kTbcParts, row = i / kTbcParts;
             const int tt = t_lo + row / c3::W, w = row % c3::W;
-            if (tt >= 0 && tt < c3::sweep(rho2))
+            if (tt >= 0 && tt < c3::nsteps(rho2))
                 cp_async_16(box + row * kTbcRow + part * 16,
-                            col + ((int64_t)(tt * c3::W + w) * 32 + l0) * c3::R + part * 16);
+                            col + ((int64_t)((tt + c3::U) * c3::W + w) * 32 + l0) * c3::R + part * 16);
         }
         cp_async_wait_all();
         __syncwarp();
@@ -128,7 +131,7 @@ __device__ void traceback_col3(const ProblemDesc &P, const IODesc &io, unsigned 
             while ((x0 | x1 | x2) != 0) {
                 const int ca = x0 / c3::WR, cb = x1 >> 5;
                 const int ll = x1 & 31, rr = x0 & (c3::R - 1), ww = (x0 % c3::WR) / c3::R;
-                const int tt = x2 + ll + rr;
+                const int tt = x2 + ll + x0 % c3::WR;
                 if (ca != cA || cb != cB || ll < l0 || ll >= l0 + kTbcLanes || tt < t_lo || tt >= t_lo + kTbcSteps)
                     break;
                 const int m = box[((tt - t_lo) * c3::W + ww) * kTbcRow + (ll - l0) * c3::R + rr];

@@ -1,255 +1,364 @@
-// k = 3 column kernel: the fill of section 2 for three sequences, organised as
-// a skewed register pipeline instead of independent tiles.
+// k = 3 column kernel: the fill of section 2 for three sequences, organised as a
+// skewed register pipeline instead of independent tiles.
 //
-// Geometry. Axis 0 (sequence 0) is split into CTA blocks of WR = W * R rows: warp
-// w of a CTA owns rows x0 = A*WR + w*R + r (r < R) in registers. Axis 1 is split
-// into blocks of 32: lane l owns x1 = 32*B + l. Axis 2 (the last, fastest axis)
-// is swept: at warp step t, lane l computes for each of its rows r the cell at
-// x2 = j = t - l - r. With this skew every predecessor of a cell was computed one
-// or two steps earlier by the same lane (rows r and r-1), by lane l-1 (received
-// with a warp shuffle), by the warp above (through a shared-memory ring), or by a
-// neighbouring CTA (through global "faces", below). The warps of a CTA run in
-// lockstep, warp w lagging warp w-1 by R steps, one __syncthreads per step.
+// Geometry (see c3:: in internal.h). A CTA owns the column (A, B): CTA rows
+// rho = w*R + r (x0 = A*WR + rho) held by warp w in registers, lanes l
+// (x1 = 32B + l), and it sweeps axis 2. At CTA time T lane l of warp w computes
+// row r's cell at x2 = T - l - rho. Then, for the cell computed at time T+1,
+//   e0  (x0-1)          is row rho-1 at time T        (same lane; warp above: ring)
+//   e2  (x2-1)          is row rho   at time T        (same lane, same register)
+//   e1  (x1-1)          is lane l-1 at time T         (shuffle at time T+1)
+//   e01, e12            are lane l-1 at time T-1      (shuffled at time T)
+//   e02                 is row rho-1 at time T-1
+//   e012                is lane l-1, row rho-1 at time T-2 (shuffled at time T-1)
+// so each step first finishes its own cells -- the max of a pre-reduced candidate
+// P and the freshly shuffled e1 candidate, then the tie-bit strip -- and then
+// prepares P for time T+1 and the e02/e012 pair D for time T+2 from values it
+// already holds. Only the shuffle, one max and the strip sit on the step-to-step
+// dependency chain.
 //
-// Faces between CTAs, written in skewed layouts so that every read and write is
-// one contiguous row:
-//   F0[cta][p + l][l]       last row of the CTA (x0 = A*WR + WR - 1) at x1 = 32B+l, x2 = p
-//   F1[cta][p + rho][rho]   last lane (x1 = 32B + 31) of CTA row rho at x2 = p
-// Every face entry is a (value, tag) pair written by one 8-byte store; the tag is
-// the launch's epoch, so a reader knows an entry is current from the entry alone
-// (no flags, no fences). A ninth "staging" warp per CTA reads the faces its CTA
-// needs from its three producer CTAs, waits (bounded) until their tags are
-// current, and copies the values into shared rings up to AHEAD chunks ahead of
-// the eight compute warps, which only ever wait on a shared counter.
+// Communication, all indexed by CTA time T (so every index inside an unrolled
+// block of U steps is a compile-time offset):
+//   ring[w][T]  row -1 of warp w at time T: (value, tag T) written by warp w-1
+//               (its last row), or by the staging warp for w = 0 (the column
+//               above, face F0 at its time T + WR). A reader accepts an entry
+//               when its tag is T, so warps never wait on a barrier.
+//   f1r[T]      lane 0's inputs from the column to the left (its lane 31 at
+//               time T + 31) and the corner from the column above-left, copied
+//               by the staging warp, which publishes how far it got.
+//   F0, F1      global faces of this column, (value, tag) 8-byte entries whose
+//               tag carries the launch epoch: no flags and no fences.
+// A column runs CTA times -U .. nsteps - 1; the first block computes cells at
+// x2 < 0 only, so that the candidates of time 0 and 1 are prepared like any
+// other (their e0/e01/e02/e012 predecessors belong to the columns above and to
+// the left). Traceback bytes and faces are stored from T = -U on (offset U).
 //
-// Cell update (packed keys, see internal.h): with pair scores scaled by 2^3,
-//   Q(x) = max( Q(x-e0), Q(x-e1), Q(x-e2),
-//               Q(x-e0-e1) + p01, Q(x-e0-e2) + p02, Q(x-e1-e2) + p12,
-//               Q(x-e0-e1-e2) + p01 + p02 + p12 )
-// then m* = (W(x) - max) mod 8 and Q(x) = max + m*; m* is the traceback byte.
-// Each lane stores its R traceback bytes of a step as one 8-byte word into the
-// column-blocked traceback layout (see c3::tb_col_bytes), 256 contiguous bytes
-// per warp step.
+// Cells outside the tensor are computed like any other. Positions x2 <= 0 take a
+// sentinel code whose pair scores are kSentinelPair, and every value starts at
+// kNeg, so such cells stay far below every valid key (the encode kernel's range
+// check keeps that margin); the origin's pre-reduced candidate is set to
+// H(0) = 0 when time 0 begins.
+//
+// Cell update with pair scores scaled by 2^3 (packed keys, see internal.h): the
+// max over the seven moves gives the key, then m* = (W(x) - max) mod 8 and
+// Q(x) = max + m*; m* is the traceback byte. Each lane stores its R bytes of a
+// step as one 4-byte word, 128 contiguous bytes per warp step.
 #include "api_internal.h"
 #include "device_common.cuh"
 
 namespace msadp {
 
 struct C3Smem {
-    int32_t ring0[c3::S][32];          // staged F0 of (A-1, B): row X at slot (X - 1) & (S - 1)
-    int32_t ringi[c3::W][c3::SI][32];  // warp w-1 -> warp w (index w >= 1), by lockstep step
-    int32_t f1[c3::S][c3::WR];         // staged F1 of (A, B-1): row X at slot X & (S - 1)
-    int32_t corner0[c3::S];            // F1 of (A-1, B-1), row X + WR - 1, entry WR - 1
-    int32_t staged;                    // chunks staged (written by the staging warp)
-    int32_t consumed;                  // chunks computed (written by compute thread 0)
-    int32_t failed;                    // a wait ran out: every warp leaves the column
-    int32_t go;                        // chunk-start decision of compute thread 0
-    int32_t ctl[4];
+    unsigned long long ring[c3::W][c3::SI][32];  // row -1 of warp w by CTA time: (value, tag)
+    int32_t f1r[c3::SF][c3::F1S];                // lane-0 inputs by CTA time: [3 + rho'], rho' = -1 .. WR-1
+    int32_t prog[c3::W];                         // compute warp w has finished the steps < prog[w]
+    int32_t staged;                              // f1r rows < staged hold this column's values
+    int32_t failed;                              // a wait ran out: every warp leaves the column
+    int32_t ctl[2];
     int32_t cur_prob;
+    int32_t pad[3];
 };
 
 int col3_warps_per_cta() { return c3::W + 1; }
 
+namespace {
+
+__device__ __forceinline__ unsigned long long pack_entry(int value, int tag) {
+    return (unsigned long long)(unsigned)value | ((unsigned long long)(unsigned)tag << 32);
+}
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long lds_u64_volatile(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.volatile.shared.u64 %0, [%1];" : "=l"(v) : "r"(smem_addr(p)));
+    return v;
+}
+__device__ __forceinline__ int ld_acquire_shared(const int32_t *p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.u32 %0, [%1];" : "=r"(v) : "r"(smem_addr(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_shared(int32_t *p, int v) {
+    asm volatile("st.release.cta.shared.u32 [%0], %1;" ::"r"(smem_addr(p)), "r"(v) : "memory");
+}
 __device__ __forceinline__ int vload(const int32_t *p) { return *reinterpret_cast<const volatile int32_t *>(p); }
 __device__ __forceinline__ void vstore(int32_t *p, int v) { *reinterpret_cast<volatile int32_t *>(p) = v; }
-__device__ __forceinline__ void compute_barrier() { asm volatile("bar.sync 1, %0;" ::"n"(c3::W * 32) : "memory"); }
-__device__ __forceinline__ int2 ld_relaxed_v2(const int32_t *p) {
-    int2 v;
-    asm volatile("ld.relaxed.gpu.global.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p) : "memory");
+// generic address: a shared ring slot or a global face entry
+__device__ __forceinline__ void st_entry(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.u64 [%0], %1;" ::"l"(p), "l"(v));
+}
+__device__ __forceinline__ void st_global_v2(unsigned long long *p, unsigned long long a, unsigned long long b) {
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b));
+}
+__device__ __forceinline__ unsigned long long ld_global_relaxed(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
     return v;
+}
+__device__ __forceinline__ ulonglong2 ld_global_relaxed_v2(const unsigned long long *p) {
+    ulonglong2 v;
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int ldtab(const char *tab, int byte_off) {
+    return *reinterpret_cast<const int *>(tab + byte_off);
+}
+
+// Mark the column failed (first failure wins the launch status).
+__device__ void c3_fail(C3Smem &sm, const LaunchDesc &L) {
+    vstore(&sm.failed, 1);
+    atomicCAS(L.err, 0, MSA_ETIMEOUT);
+}
+
+// Slow path of a ring read: wait (bounded) until every lane's entry carries tag T.
+__device__ __noinline__ unsigned long long c3_ring_wait(const unsigned long long *p, int T, C3Smem &sm,
+                                                       const LaunchDesc &L) {
+    const uint64_t t0 = global_ns();
+    unsigned long long e = lds_u64_volatile(p);
+    while (__any_sync(kFull, (int)(e >> 32) != T)) {
+        if (vload(&sm.failed) || (int64_t)(global_ns() - t0) > L.spin_ns) {
+            if ((threadIdx.x & 31) == 0) c3_fail(sm, L);
+            return pack_entry(kNeg, T);
+        }
+        __nanosleep(20);
+        e = lds_u64_volatile(p);
+    }
+    return e;
+}
+
+// Registers of one compute lane that change from step to step.
+struct C3St {
+    int V[c3::R];       // V(T-1, r) on entry to step T, V(T, r) after it
+    int P[c3::R];       // max over every candidate of cell (T, r) but e1
+    int D[c3::R];       // max of the e02 and e012 candidates of cell (T+1, r)
+    int cc[2 * c3::R];  // byte offsets of axis-2 codes: shift register by position
+    int pp[2 * c3::R];  // pair scores (x1, x2) of those positions
+    int VM;             // V(T-1, -1): the ring entry of the previous step
+};
+
+// Constants of one compute lane for a column.
+struct C3Ln {
+    int p01[c3::R];     // pair score (x0, x1) per row
+    int rowb[c3::R];    // byte offset of row r's table row (code of x0) plus 4 * lane
+    int laneb;          // byte offset of this lane's table row (code of x1) plus 4 * lane
+    int Wl;             // W(x) = Wl + 4T - 3r
+    int wR;             // first CTA row of the warp
+    int tagout;         // tag base of ring-out entries (0: shared ring, epoch << 16: global face)
+    int tagf1;          // tag base of this column's F1 entries
+    bool last;          // lane 31 writes the F1 face
+};
+
+// Per-block addresses (block = U steps starting at CTA time T0).
+struct C3Blk {
+    const unsigned long long *rin;  // ring[w][T0 mod SI][lane]
+    unsigned long long *rout;       // ring[w+1][T0 mod SI][lane] or F0[T0][lane] (generic)
+    const int *f1row;               // f1r[T0 mod SF]
+    unsigned *tbp;                  // traceback word of (T0, w, lane)
+    unsigned long long *f1o;        // F1[T0][wR]
+    const uint16_t *c2p;            // code offset of x2 = T0 + 2 - lane - wR
+};
+
+template <int s>
+__device__ __forceinline__ void c3_step(C3St &g, const C3Ln &c, const char *tab, const C3Blk &b, int T0, int lane,
+                                        C3Smem &sm, const LaunchDesc &L) {
+    constexpr int M = 2 * c3::R - 1;
+    constexpr int R = c3::R;
+    const int T = T0 + s;
+    // U(T, r) from lane l-1 (lane 0: the staged face)
+    const int *fr = b.f1row + s * c3::F1S;
+    const int4 f = *reinterpret_cast<const int4 *>(fr + 4 + c.wR);
+    const int fm = fr[3 + c.wR];
+    const int fv[4] = {f.x, f.y, f.z, f.w};
+    int Un[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int v = __shfl_up_sync(kFull, g.V[r], 1);
+        Un[r] = lane == 0 ? fv[r] : v;
+    }
+    int UMn = __shfl_up_sync(kFull, g.VM, 1);
+    if (lane == 0) UMn = fm;
+    // the cells of time T
+    const int WT = c.Wl + 4 * T;
+    unsigned pk = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int acc = max(g.P[r], Un[r]);
+        const int m = (WT - 3 * r - acc) & 7;
+        g.V[r] = acc + m;
+        pk |= (unsigned)m << (8 * r);
+    }
+    // outputs: last row to the warp below (or face F0), traceback bytes, lane 31 to face F1
+    st_entry(b.rout + s * 32, pack_entry(g.V[R - 1], c.tagout + T));
+    b.tbp[s * (c3::W * 32)] = pk;
+    if (c.last) {
+        const int tg = c.tagf1 + T;
+        st_global_v2(b.f1o + s * c3::WR, pack_entry(g.V[0], tg), pack_entry(g.V[1], tg));
+        st_global_v2(b.f1o + s * c3::WR + 2, pack_entry(g.V[2], tg), pack_entry(g.V[3], tg));
+    }
+    // code of the position x2 = T + 2 - lane - wR (row 0 of time T + 2)
+    const int cn = b.c2p[s];
+    g.cc[s & M] = cn;
+    g.pp[s & M] = ldtab(tab, c.laneb + cn);
+    // row -1: V(T, -1) from the ring (written by the warp above at its time T)
+    unsigned long long e = lds_u64_volatile(b.rin + s * 32);
+    if (__any_sync(kFull, (int)(e >> 32) != T)) e = c3_ring_wait(b.rin + s * 32, T, sm, L);
+    const int VMn = (int)(unsigned)e;
+    // P of time T + 1 and D of time T + 2
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int vm = r ? g.V[r - 1] : VMn;
+        const int um = r ? Un[r - 1] : UMn;
+        const int y = um + c.p01[r];
+        int pn = max(max(g.D[r], vm), max(g.V[r], y));
+        pn = max(pn, Un[r] + g.pp[(s - r - 1) & M]);
+        const int p02 = ldtab(tab, c.rowb[r] + g.cc[(s - r) & M]);
+        const int p12 = g.pp[(s - r) & M];
+        g.D[r] = max(vm + p02, y + p02 + p12);
+        g.P[r] = pn;
+    }
+    g.VM = VMn;
 }
 
 struct C3Col {
-    int A, B, nsteps, TS;
-    int rho0, rho1, rho2, len2;
-    const int32_t *f0src, *f1src, *c0src;  // producer faces (nullptr: none)
-    int32_t *f0dst, *f1dst;                // this column's faces
+    int A, B, N;
+    const unsigned long long *f0up, *f1left, *f1diag;  // producer faces (nullptr: none)
+    unsigned long long *f0dst, *f1dst;                  // this column's faces
+    int tagbase;                                        // (epoch << 16) of this launch
 };
 
-// Staging warp: copy chunk c's face entries into the shared rings once every
-// needed entry carries this launch's tag. Entries outside the tensor (position
-// p < 0 or p >= rho2) are never needed and are staged as "no predecessor".
-// Returns false when the wait runs out or another warp gave up.
-__device__ bool c3_stage_chunk(C3Smem &sm, const C3Col &cc, int c, int lane, int epoch, const LaunchDesc &L) {
-    const int T0 = c * c3::CH;
+// Staging warp: copy the column's inputs from the producer columns' faces into
+// ring[0] and f1r, as soon as their tags show this launch's values, and publish
+// the number of CTA-time rows staged. Positions a producer never computes (past
+// its last step, or no producer at all) are staged as kNeg. A batch covers SB
+// rows: every load of the batch is issued before any tag is checked (one L2 round
+// trip per batch); a face row is 32 entries of 8 bytes, read by half a warp as
+// 16-byte pairs, so one load instruction covers two rows.
+__device__ void c3_stager(C3Smem &sm, const C3Col &cc, int lane, const LaunchDesc &L) {
+    constexpr int SB = 16;                 // rows per batch
+    constexpr int NL = SB / 2;             // vector loads per face and lane
+    static_assert(SB <= c3::SI - c3::U && SB <= c3::SF - c3::U, "staging batch exceeds the rings");
+    const int half = lane >> 4, pair = 2 * (lane & 15);  // row parity and first entry of this lane
+    int Ts = -c3::U;
+    uint64_t t_progress = global_ns();
+    while (Ts < cc.N) {
+        // the slots to fill must have been read by the compute warps
+        {
+            const int need0 = Ts + SB - c3::SI, needall = Ts + SB - c3::SF;
+            int ok;
+            while (true) {
+                const int pw = lane < c3::W ? ld_acquire_shared(&sm.prog[lane]) : (1 << 30);
+                const int pmin = __reduce_min_sync(kFull, pw);
+                const int p0 = __shfl_sync(kFull, pw, 0);
+                ok = p0 >= need0 && pmin >= needall;
+                if (ok) break;
+                if (vload(&sm.failed) || (int64_t)(global_ns() - t_progress) > L.spin_ns) break;
+                __nanosleep(64);
+            }
+            if (!ok) {
+                if (lane == 0 && !vload(&sm.failed)) c3_fail(sm, L);
+                return;
+            }
+        }
+        // issue every load of the batch
+        ulonglong2 a[NL], b[NL];
+        unsigned long long d = pack_entry(kNeg, 0);
+        const ulonglong2 none = make_ulonglong2(pack_entry(kNeg, 0), pack_entry(kNeg, 0));
+#pragma unroll
+        for (int i = 0; i < NL; ++i) {
+            const int T = Ts + 2 * i + half;
+            a[i] = none;
+            b[i] = none;
+            if (cc.f0up && T + c3::WR < cc.N)
+                a[i] = ld_global_relaxed_v2(cc.f0up + (int64_t)(T + c3::WR + c3::U) * 32 + pair);
+            if (cc.f1left && T + 31 < cc.N)
+                b[i] = ld_global_relaxed_v2(cc.f1left + (int64_t)(T + 31 + c3::U) * c3::WR + pair);
+        }
+        {
+            const int T = Ts + lane;  // lane i fetches the corner of row Ts + i
+            if (lane < SB && cc.f1diag && T + 31 + c3::WR < cc.N)
+                d = ld_global_relaxed(cc.f1diag + (int64_t)(T + 31 + c3::WR + c3::U) * c3::WR + c3::WR - 1);
+        }
+        // rows whose entries all carry this launch's tag
+        unsigned rows_ok = 0;
+#pragma unroll
+        for (int i = 0; i < NL; ++i) {
+            const int T = Ts + 2 * i + half;
+            bool v = true;
+            if (cc.f0up && T + c3::WR < cc.N) {
+                const int want = cc.tagbase + T + c3::WR;
+                v = v && (int)(a[i].x >> 32) == want && (int)(a[i].y >> 32) == want;
+            }
+            if (cc.f1left && T + 31 < cc.N) {
+                const int want = cc.tagbase + T + 31;
+                v = v && (int)(b[i].x >> 32) == want && (int)(b[i].y >> 32) == want;
+            }
+            const unsigned bal = __ballot_sync(kFull, v);
+            rows_ok |= ((bal & 0xffffu) == 0xffffu ? 1u : 0u) << (2 * i);
+            rows_ok |= ((bal >> 16) == 0xffffu ? 1u : 0u) << (2 * i + 1);
+        }
+        {
+            const int T = Ts + lane;
+            const bool v = lane >= SB || !cc.f1diag || T + 31 + c3::WR >= cc.N ||
+                           (int)(d >> 32) == cc.tagbase + T + 31 + c3::WR;
+            rows_ok &= __ballot_sync(kFull, v) & ((1u << SB) - 1);
+        }
+        const int n = rows_ok == (1u << SB) - 1 ? SB : __ffs(~rows_ok) - 1;  // rows ready, in order
+#pragma unroll
+        for (int i = 0; i < NL; ++i) {
+            const int r = 2 * i + half;
+            if (r < n) {
+                const int T = Ts + r;
+                *reinterpret_cast<ulonglong2 *>(&sm.ring[0][T & (c3::SI - 1)][pair]) =
+                    make_ulonglong2(pack_entry((int)(unsigned)a[i].x, T), pack_entry((int)(unsigned)a[i].y, T));
+                *reinterpret_cast<int2 *>(&sm.f1r[T & (c3::SF - 1)][4 + pair]) =
+                    make_int2((int)(unsigned)b[i].x, (int)(unsigned)b[i].y);
+            }
+        }
+        if (lane < n) sm.f1r[(Ts + lane) & (c3::SF - 1)][3] = (int)(unsigned)d;
+        if (n > 0) {
+            Ts += n;
+            __syncwarp();
+            if (lane == 0) st_release_shared(&sm.staged, Ts);
+            t_progress = global_ns();
+        } else {
+            if (vload(&sm.failed) || ld_volatile(L.err) != 0 || (int64_t)(global_ns() - t_progress) > L.spin_ns) {
+                if (lane == 0 && !vload(&sm.failed)) c3_fail(sm, L);
+                return;
+            }
+            __nanosleep(64);
+        }
+    }
+}
+
+// Block prologue of a compute warp: publish progress, then wait (bounded) until
+// the staged face covers the block and the warp below has freed the ring slots.
+__device__ __forceinline__ bool c3_block_wait(C3Smem &sm, int w, int T0, const LaunchDesc &L) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) st_release_shared(&sm.prog[w], T0);
+    const int need_st = T0 + c3::U;
+    const int need_dn = T0 + c3::U - c3::SI;
+    const bool lastw = w == c3::W - 1;
+    if (ld_acquire_shared(&sm.staged) >= need_st && (lastw || ld_acquire_shared(&sm.prog[w + 1]) >= need_dn))
+        return true;
     const uint64_t t0 = global_ns();
-    for (uint32_t it = 0;; ++it) {
-        constexpr int H = (c3::WR + 31) / 32;  // F1 entries per lane and row
-        int f0v[c3::CH], f1v[c3::CH][H], cv = kNeg;
-        bool ok = true;
-#pragma unroll
-        for (int i = 0; i < c3::CH; ++i) {
-            const int X = T0 + i;
-            // F0 entry (X, lane): position X - lane
-            int v = kNeg;
-            if (cc.f0src && (unsigned)(X - lane) < (unsigned)cc.rho2) {
-                const int2 e = ld_relaxed_v2(cc.f0src + (int64_t)X * c3::F0W + 2 * lane);
-                ok = ok && e.y == epoch;
-                v = e.x;
-            }
-            f0v[i] = v;
-#pragma unroll
-            for (int h = 0; h < H; ++h) {
-                const int rho = lane + 32 * h;  // F1 entry (X, rho): position X - rho
-                int u = kNeg;
-                if (cc.f1src && rho < c3::WR && (unsigned)(X - rho) < (unsigned)cc.rho2) {
-                    const int2 e = ld_relaxed_v2(cc.f1src + (int64_t)X * c3::F1W + 2 * rho);
-                    ok = ok && e.y == epoch;
-                    u = e.x;
-                }
-                f1v[i][h] = u;
-            }
-        }
-        if (lane < c3::CH) {  // corner: F1 of (A-1, B-1) row X + WR - 1, entry WR - 1: position X
-            const int X = T0 + lane;
-            if (cc.c0src && (unsigned)X < (unsigned)cc.rho2) {
-                const int2 e = ld_relaxed_v2(cc.c0src + (int64_t)(X + c3::WR - 1) * c3::F1W + 2 * (c3::WR - 1));
-                ok = ok && e.y == epoch;
-                cv = e.x;
-            }
-        }
-        if (__all_sync(kFull, ok)) {
-#pragma unroll
-            for (int i = 0; i < c3::CH; ++i) {
-                const int X = T0 + i;
-                sm.ring0[(X - 1) & (c3::S - 1)][lane] = f0v[i];
-#pragma unroll
-                for (int h = 0; h < H; ++h)
-                    if (lane + 32 * h < c3::WR) sm.f1[X & (c3::S - 1)][lane + 32 * h] = f1v[i][h];
-            }
-            if (lane < c3::CH) sm.corner0[(T0 + lane) & (c3::S - 1)] = cv;
+    while (true) {
+        __nanosleep(32);
+        if (ld_acquire_shared(&sm.staged) >= need_st && (lastw || ld_acquire_shared(&sm.prog[w + 1]) >= need_dn))
             return true;
+        if (vload(&sm.failed)) return false;
+        if ((int64_t)(global_ns() - t0) > L.spin_ns) {
+            if ((threadIdx.x & 31) == 0) c3_fail(sm, L);
+            return false;
         }
-        if ((it & 7) == 7) {
-            if (vload(&sm.failed) || ld_volatile(L.err) != 0) return false;
-            if ((int64_t)(global_ns() - t0) > L.spin_ns) return false;
-        }
-        __nanosleep(128);
     }
 }
 
-// Per-warp register state of one column.
-struct C3Regs {
-    int V[3][c3::R];   // own values by generation (step mod 3)
-    int U[3][c3::R];   // values received from lane l-1
-    int VM[3], UM[3];  // row -1 (warp above), own lane and lane l-1
-    int code[c3::R];   // axis-2 code of each row's current position
-};
-
-// Column-constant inputs of a compute warp.
-struct C3Lane {
-    const int *tabr;          // replicated pair table
-    int rowoff[c3::R];        // byte offset of row r's table row (code of x0) in tabr
-    int laneoff;              // byte offset of this lane's table row (code of x1)
-    int p01[c3::R];           // scaled pair score of (x0, x1) per row
-    int Wb;                   // W(x) = Wb - 3 r + 4 t for row r at warp step t
-    const unsigned char *sc2; // axis-2 codes, indexed by position
-    const int32_t *vmring;    // row -1 source: staged face (warp 0) or the warp above
-    int vmask;
-    unsigned char *tbw;       // this lane's traceback bytes at warp step 0
-    int32_t *f0dst, *f1dst;
-    int lane, w, rho2, TS, tag;
-    bool origin;
-};
-
-template <bool MASK, int s>
-__device__ __forceinline__ void c3_step(C3Regs &g, C3Smem &sm, const C3Lane &c, int T, int t) {
-    constexpr int cur = s % 3, prv = (s + 2) % 3, pv2 = (s + 1) % 3;
-    const int lane = c.lane, w = c.w;
-    // receive lane l-1's values of the previous step; lane 0 takes the axis-1 face
-    const int4 fa = *reinterpret_cast<const int4 *>(&sm.f1[T & (c3::S - 1)][w * c3::R]);
-    const int4 fb = *reinterpret_cast<const int4 *>(&sm.f1[T & (c3::S - 1)][w * c3::R + 4]);
-    const int fl[8] = {fa.x, fa.y, fa.z, fa.w, fb.x, fb.y, fb.z, fb.w};
-#pragma unroll
-    for (int r = 0; r < c3::R; ++r) {
-        const int v = __shfl_up_sync(kFull, g.V[prv][r], 1);
-        g.U[cur][r] = lane == 0 ? fl[r] : v;
-    }
-    // row -1 from the warp above (or the staged face of CTA (A-1, B))
-    g.VM[cur] = c.vmring[((T - 1) & c.vmask) * 32 + lane];
-    {
-        const int um = c.vmring[((T - 2) & c.vmask) * 32 + ((lane + 31) & 31)];
-        const int cw = w == 0 ? sm.corner0[T & (c3::S - 1)] : sm.f1[(T - 1) & (c3::S - 1)][w * c3::R - 1];
-        g.UM[cur] = lane == 0 ? cw : um;
-    }
-    // shift the per-row axis-2 codes: row r now sits one position behind row r-1
-#pragma unroll
-    for (int r = c3::R - 1; r > 0; --r) g.code[r] = g.code[r - 1];
-    g.code[0] = c.sc2[t - lane];
-    const int w4 = c.Wb + 4 * t;
-    const int jl = t - lane;
-    int m8[c3::R];
-#pragma unroll
-    for (int r = 0; r < c3::R; ++r) {
-        const int c2 = g.code[r] << 7;  // table stride per code: 32 lanes * 4 bytes
-        const char *tb = reinterpret_cast<const char *>(c.tabr);
-        const int p02 = *reinterpret_cast<const int *>(tb + c.rowoff[r] + c2);
-        const int p12 = *reinterpret_cast<const int *>(tb + c.laneoff + c2);
-        const int v1m = r == 0 ? g.VM[cur] : g.V[prv][r - 1];
-        const int v2m = r == 0 ? g.VM[prv] : g.V[pv2][r - 1];
-        const int u1m = r == 0 ? g.UM[cur] : g.U[prv][r - 1];
-        const int u2m = r == 0 ? g.UM[prv] : g.U[pv2][r - 1];
-        // max over the seven moves, as a balanced tree
-        const int a = max(v1m, g.U[cur][r]);
-        const int b = max(g.V[prv][r], u1m + c.p01[r]);
-        const int d = max(v2m + p02, g.U[prv][r] + p12);
-        const int e = u2m + (c.p01[r] + p02 + p12);
-        const int acc = max(max(a, b), max(d, e));
-        // strip the tie bits: Q = W + ceil8(acc - W), m* = Q - acc
-        const int wx = w4 - 3 * r;
-        int q = ((acc - wx + 7) & ~7) + wx;
-        int m = q - acc;
-        if (MASK) {
-            const bool valid = (unsigned)(jl - r) < (unsigned)c.rho2;
-            q = valid ? q : kNeg;
-            if (r == 0 && c.origin && jl == 0) {  // H(0) = 0, no move
-                q = 0;
-                m = 0;
-            }
-        }
-        g.V[cur][r] = q;
-        m8[r] = m;
-    }
-    // traceback bytes of the 8 rows: one 8-byte store per lane, 256 B per warp
-    {
-        const unsigned lo = (unsigned)m8[0] | (unsigned)m8[1] << 8 | (unsigned)m8[2] << 16 | (unsigned)m8[3] << 24;
-        const unsigned hi = (unsigned)m8[4] | (unsigned)m8[5] << 8 | (unsigned)m8[6] << 16 | (unsigned)m8[7] << 24;
-        *reinterpret_cast<uint2 *>(c.tbw + (int64_t)t * (c3::W * 32 * c3::R)) = make_uint2(lo, hi);
-    }
-    // faces: last row of the warp feeds the warp below; last lane feeds CTA (A, B+1)
-    if (w + 1 < c3::W) {
-        sm.ringi[w + 1][T & (c3::SI - 1)][lane] = g.V[cur][c3::R - 1];
-    } else if (T - c3::WR + 1 >= 0) {
-        *reinterpret_cast<int2 *>(c.f0dst + (int64_t)(T - c3::WR + 1) * c3::F0W + 2 * lane) =
-            make_int2(g.V[cur][c3::R - 1], c.tag);
-    }
-    if (lane == 31 && T >= 31) {
-        int4 *d = reinterpret_cast<int4 *>(c.f1dst + (int64_t)(T - 31) * c3::F1W + 2 * w * c3::R);
-        d[0] = make_int4(g.V[cur][0], c.tag, g.V[cur][1], c.tag);
-        d[1] = make_int4(g.V[cur][2], c.tag, g.V[cur][3], c.tag);
-        d[2] = make_int4(g.V[cur][4], c.tag, g.V[cur][5], c.tag);
-        d[3] = make_int4(g.V[cur][6], c.tag, g.V[cur][7], c.tag);
-    }
-}
-
-template <bool MASK>
-__device__ __forceinline__ void c3_chunk(C3Regs &g, C3Smem &sm, const C3Lane &c, int T0) {
-#define C3_STEP(s)                                            \
-    {                                                         \
-        const int T = T0 + (s), t = T - c.w * c3::R;          \
-        if (t >= 0 && t < c.TS) c3_step<MASK, (s)>(g, sm, c, T, t); \
-        compute_barrier();                                    \
-    }
-    C3_STEP(0) C3_STEP(1) C3_STEP(2) C3_STEP(3) C3_STEP(4) C3_STEP(5)
-    C3_STEP(6) C3_STEP(7) C3_STEP(8) C3_STEP(9) C3_STEP(10) C3_STEP(11)
-#undef C3_STEP
-}
+}  // namespace
 
 __global__ void __launch_bounds__(c3::THREADS, 1) fill_col3_kernel(const LaunchDesc L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C3Smem &sm = *reinterpret_cast<C3Smem *>(smem_raw);
     int *tabr = reinterpret_cast<int *>(smem_raw + sizeof(C3Smem));
-    unsigned char *sc2base = reinterpret_cast<unsigned char *>(tabr + L.tab_ints);  // axis-2 codes
+    uint16_t *c2off = reinterpret_cast<uint16_t *>(tabr + L.tab_ints);  // axis-2 code offsets by x2 + CODEPAD
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const bool stager = w == c3::W;
@@ -276,155 +385,123 @@ __global__ void __launch_bounds__(c3::THREADS, 1) fill_col3_kernel(const LaunchD
         C3Col cc;
         cc.A = lin / NB;
         cc.B = lin - cc.A * NB;
-        cc.rho0 = P.rho[0];
-        cc.rho1 = P.rho[1];
-        cc.rho2 = P.rho[2];
-        cc.len2 = P.len[2];
-        cc.TS = cc.rho2 + c3::R + 31 + c3::EXTRA;
-        cc.nsteps = c3::nsteps(cc.rho2);
-        const int nchunks = cc.nsteps / c3::CH;
-        cc.f0dst = P.Q + (int64_t)lin * P.face0_stride;
-        cc.f1dst = P.aux + (int64_t)lin * P.face1_stride;
-        cc.f0src = cc.A > 0 ? P.Q + (int64_t)(lin - NB) * P.face0_stride : nullptr;
-        cc.f1src = cc.B > 0 ? P.aux + (int64_t)(lin - 1) * P.face1_stride : nullptr;
-        cc.c0src = (cc.A > 0 && cc.B > 0) ? P.aux + (int64_t)(lin - NB - 1) * P.face1_stride : nullptr;
+        cc.N = c3::nsteps(P.rho[2]);
+        const int64_t f0s = P.face0_stride / 2, f1s = P.face1_stride / 2;  // entries per column face
+        unsigned long long *F0 = reinterpret_cast<unsigned long long *>(P.Q);
+        unsigned long long *F1 = reinterpret_cast<unsigned long long *>(P.aux);
+        cc.f0dst = F0 + (int64_t)lin * f0s;
+        cc.f1dst = F1 + (int64_t)lin * f1s;
+        cc.f0up = cc.A > 0 ? F0 + (int64_t)(lin - NB) * f0s : nullptr;
+        cc.f1left = cc.B > 0 ? F1 + (int64_t)(lin - 1) * f1s : nullptr;
+        cc.f1diag = (cc.A > 0 && cc.B > 0) ? F1 + (int64_t)(lin - NB - 1) * f1s : nullptr;
+        cc.tagbase = L.epoch << 16;
         // a withheld column (test hook) writes faces no reader accepts
-        const int tag = (int64_t)ticket == L.withhold ? 0 : L.epoch;
+        const int tag_faces = (int64_t)ticket == L.withhold ? 0 : cc.tagbase;
 
         const int A = P.A;
-        // replicated pair table (entry-major, one copy per lane) and axis-2 codes
+        // replicated pair table (entry-major, one copy per lane) with a sentinel
+        // code A for positions x2 <= 0, and the axis-2 code offsets
         const int have = sm.cur_prob;
         __syncthreads();
         if (have != pidx)
-            for (int i = tid; i < A * A * 32; i += c3::THREADS) tabr[i] = P.tab[i >> 5];
+            for (int i = tid; i < A * (A + 1) * 32; i += c3::THREADS) {
+                const int c0 = i / ((A + 1) * 32), c2 = (i >> 5) % (A + 1);
+                tabr[i] = c2 == A ? c3::kSentinelPair : P.tab[c0 * A + c2];
+            }
         if (tid == 0) {
             sm.cur_prob = pidx;
-            sm.staged = 0;
-            sm.consumed = 0;
+            sm.staged = -c3::U;
             sm.failed = 0;
         }
-        for (int i = tid; i < cc.rho2 + 2 * c3::CODEPAD + 32; i += c3::THREADS) {
-            const int j = i - c3::CODEPAD;  // position x2 = j consumes residue j - 1
-            sc2base[i] = (j >= 1 && j <= cc.len2) ? P.codes[P.cofs[2] + j - 1] : (unsigned char)0;
+        if (tid < c3::W) sm.prog[tid] = -c3::U;
+        const int len2 = P.len[2];
+        for (int i = tid; i < P.rho[2] + 2 * c3::CODEPAD + 16; i += c3::THREADS) {
+            const int x2 = i - c3::CODEPAD;  // position x2 consumes residue x2 - 1
+            const int code = x2 <= 0 ? A : x2 <= len2 ? P.codes[P.cofs[2] + x2 - 1] : 0;
+            c2off[i] = (uint16_t)(code * 128);
         }
-        // rings start at "no predecessor"
-        for (int i = tid; i < c3::S * 32; i += c3::THREADS) (&sm.ring0[0][0])[i] = kNeg;
-        for (int i = tid; i < c3::W * c3::SI * 32; i += c3::THREADS) (&sm.ringi[0][0][0])[i] = kNeg;
-        for (int i = tid; i < c3::S * c3::WR; i += c3::THREADS) (&sm.f1[0][0])[i] = kNeg;
-        for (int i = tid; i < c3::S; i += c3::THREADS) sm.corner0[i] = kNeg;
+        // ring entries start with a tag no step uses
+        for (int i = tid; i < c3::W * c3::SI * 32; i += c3::THREADS)
+            (&sm.ring[0][0][0])[i] = pack_entry(kNeg, 0x7fffffff);
         __syncthreads();
 
         if (stager) {
-            for (int c = 0; c < nchunks; ++c) {
-                // back-pressure: at most AHEAD chunks beyond the compute warps
-                const uint64_t t0 = global_ns();
-                bool ok = true;
-                while (vload(&sm.consumed) <= c - c3::AHEAD) {
-                    if (vload(&sm.failed) || ld_volatile(L.err) != 0 ||
-                        (int64_t)(global_ns() - t0) > L.spin_ns) {
-                        ok = false;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-                ok = ok && c3_stage_chunk(sm, cc, c, lane, L.epoch, L);
-                if (!ok) {
-                    if (lane == 0) {
-                        vstore(&sm.failed, 1);
-                        atomicCAS(L.err, 0, MSA_ETIMEOUT);
-                    }
-                    break;
-                }
-                __syncwarp();
-                __threadfence_block();
-                if (lane == 0) vstore(&sm.staged, c + 1);
-            }
+            c3_stager(sm, cc, lane, L);
         } else {
-            // column constants of this lane
-            C3Lane cl;
-            cl.lane = lane;
-            cl.w = w;
-            cl.rho2 = cc.rho2;
-            cl.TS = cc.TS;
-            cl.tag = tag;
-            cl.tabr = tabr;
-            cl.f0dst = cc.f0dst;
-            cl.f1dst = cc.f1dst;
+            const bool lastw = w == c3::W - 1;
+            C3Ln c;
+            c.wR = w * c3::R;
+            c.last = lane == 31;
+            c.tagout = lastw ? tag_faces : 0;
+            c.tagf1 = tag_faces;
             const int x1 = cc.B * 32 + lane;
             const int code1 = (x1 >= 1 && x1 <= P.len[1]) ? P.codes[P.cofs[1] + x1 - 1] : 0;
-            const int x0b = cc.A * c3::WR + w * c3::R;
+            const int x0b = cc.A * c3::WR + c.wR;
 #pragma unroll
             for (int r = 0; r < c3::R; ++r) {
                 const int x0 = x0b + r;
                 const int code0 = (x0 >= 1 && x0 <= P.len[0]) ? P.codes[P.cofs[0] + x0 - 1] : 0;
-                cl.rowoff[r] = (code0 * A * 32 + lane) * 4;
-                cl.p01[r] = P.tab[code0 * A + code1];
+                c.rowb[r] = (code0 * (A + 1) * 32 + lane) * 4;
+                c.p01[r] = P.tab[code0 * A + code1];
             }
-            cl.laneoff = (code1 * A * 32 + lane) * 4;
-            // W(x) = x0 + 2 x1 + 4 x2 with x0 = x0b + r, x2 = t - lane - r
-            cl.Wb = x0b + 2 * x1 - 4 * lane;
-            cl.tbw = P.tb + (int64_t)lin * c3::tb_col_bytes(cc.rho2) + (int64_t)(w * 32 + lane) * c3::R;
-            cl.vmring = w == 0 ? &sm.ring0[0][0] : &sm.ringi[w][0][0];
-            cl.vmask = w == 0 ? c3::S - 1 : c3::SI - 1;
-            cl.sc2 = sc2base + c3::CODEPAD;
-            cl.origin = cc.A == 0 && cc.B == 0 && w == 0 && lane == 0;
+            c.laneb = (code1 * (A + 1) * 32 + lane) * 4;
+            c.Wl = cc.A * c3::WR + 64 * cc.B - 2 * lane - 3 * c.wR;
+            const char *tab = reinterpret_cast<const char *>(tabr);
+            const uint16_t *c2lane = c2off + c3::CODEPAD + 2 - lane - c.wR;  // x2 = T + 2 - lane - wR at T
 
-            C3Regs g;
+            C3St g;
 #pragma unroll
             for (int r = 0; r < c3::R; ++r) {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    g.V[k][r] = kNeg;
-                    g.U[k][r] = kNeg;
-                }
-                g.code[r] = 0;
+                g.V[r] = kNeg;
+                g.P[r] = kNeg;
+                g.D[r] = kNeg;
             }
+            const bool origin = cc.A == 0 && cc.B == 0 && w == 0 && lane == 0;
+            g.VM = kNeg;
+            // shift registers before time -U: positions x2 = 2 - U - lane - wR - j, j = 1 .. 2R-1
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                g.VM[k] = kNeg;
-                g.UM[k] = kNeg;
+            for (int j = 1; j < 2 * c3::R; ++j) {
+                const int cj = c2lane[-c3::U - j];
+                g.cc[(-j) & (2 * c3::R - 1)] = cj;
+                g.pp[(-j) & (2 * c3::R - 1)] = ldtab(tab, c.laneb + cj);
             }
+            g.cc[0] = g.pp[0] = 0;
 
-            for (int c = 0; c < nchunks; ++c) {
-                if (tid == 0) {
-                    const uint64_t t0 = global_ns();
-                    int go = 1;
-                    while (vload(&sm.staged) <= c) {
-                        if (vload(&sm.failed) || (int64_t)(global_ns() - t0) > L.spin_ns) {
-                            go = 0;
-                            break;
-                        }
-                        __nanosleep(32);
-                    }
-                    if (!go) {
-                        vstore(&sm.failed, 1);
-                        atomicCAS(L.err, 0, MSA_ETIMEOUT);
-                    }
-                    sm.go = go;
-                }
-                compute_barrier();
-                if (!sm.go) break;
-                __threadfence_block();
-                const int T0 = c * c3::CH;
-                const int t0 = T0 - w * c3::R;
-                // interior chunk for this warp: every (lane, row) position inside [1, rho2)
-                const bool interior = t0 - 31 - (c3::R - 1) >= 1 && t0 + c3::CH - 1 <= cc.rho2 - 1;
-                if (interior)
-                    c3_chunk<false>(g, sm, cl, T0);
-                else
-                    c3_chunk<true>(g, sm, cl, T0);
-                if (tid == 0) vstore(&sm.consumed, c + 1);
+            unsigned long long *ringout = lastw ? cc.f0dst + lane : &sm.ring[w + 1][0][lane];
+            unsigned *tbw = reinterpret_cast<unsigned *>(P.tb + (int64_t)lin * c3::tb_col_bytes(P.rho[2])) +
+                            w * 32 + lane;
+            for (int T0 = -c3::U; T0 < cc.N; T0 += c3::U) {
+                if (!c3_block_wait(sm, w, T0, L)) break;
+                if (T0 == 0 && origin) g.P[0] = 0;  // H(0) = 0, no move
+                C3Blk b;
+                b.rin = &sm.ring[w][T0 & (c3::SI - 1)][lane];
+                b.rout = lastw ? ringout + (int64_t)(T0 + c3::U) * 32 : ringout + (T0 & (c3::SI - 1)) * 32;
+                b.f1row = &sm.f1r[T0 & (c3::SF - 1)][0];
+                b.tbp = tbw + (int64_t)(T0 + c3::U) * (c3::W * 32);
+                b.f1o = cc.f1dst + (int64_t)(T0 + c3::U) * c3::WR + c.wR;
+                b.c2p = c2lane + T0;
+                c3_step<0>(g, c, tab, b, T0, lane, sm, L);
+                c3_step<1>(g, c, tab, b, T0, lane, sm, L);
+                c3_step<2>(g, c, tab, b, T0, lane, sm, L);
+                c3_step<3>(g, c, tab, b, T0, lane, sm, L);
+                c3_step<4>(g, c, tab, b, T0, lane, sm, L);
+                c3_step<5>(g, c, tab, b, T0, lane, sm, L);
+                c3_step<6>(g, c, tab, b, T0, lane, sm, L);
+                c3_step<7>(g, c, tab, b, T0, lane, sm, L);
             }
+            __syncwarp();
+            if (lane == 0) st_release_shared(&sm.prog[w], 1 << 30);
         }
         __syncthreads();
         if (vload(&sm.failed)) break;
     }
 }
 
-// Dynamic shared memory: rings and face staging, the replicated pair table
-// (A*A entries x 32 lanes) and the padded axis-2 codes.
+// Dynamic shared memory: rings and staged faces, the replicated pair table with
+// its sentinel column (A*(A+1) entries x 32 lanes) and the axis-2 code offsets.
 int col3_smem_bytes(int alphabet_size) {
-    return (int)sizeof(C3Smem) + alphabet_size * alphabet_size * 32 * 4 + c3::MAXRHO2 + 2 * c3::CODEPAD + 48;
+    return (int)sizeof(C3Smem) + alphabet_size * (alphabet_size + 1) * 32 * 4 +
+           (c3::MAXRHO2 + 2 * c3::CODEPAD + 16) * 2 + 16;
 }
 
 int fill_col3_ctas_per_sm(int smem) {

@@ -99,36 +99,48 @@ __host__ __device__ constexpr int tile_extent(int k, int i) {
 }
 
 // k = 3 column kernel geometry (shared by the planner and the kernel).
+//
+// A CTA owns a column: rows x0 in [A*WR, A*WR + WR) (warp w holds rows
+// w*R .. w*R + R - 1 in registers), lanes x1 in [32B, 32B + 32), and sweeps axis
+// 2. All of its warps share one clock, the CTA time T: at time T lane l of warp
+// w computes, for each of its rows r, the cell with CTA row rho = w*R + r at
+// x2 = T - l - rho. Every predecessor of that cell is then produced at time T-1
+// or T-2 (same lane, lane l-1, or row rho-1), so rings indexed by T connect the
+// warps of a CTA and faces indexed by T connect neighbouring columns.
 namespace c3 {
-constexpr int R = 8;         // rows per warp along axis 0 (registers)
-constexpr int W = 4;         // compute warps per CTA, stacked along axis 0 (one per SM sub-partition)
-constexpr int WR = R * W;    // rows per CTA
-constexpr int CH = 12;       // lockstep steps per chunk (staging granularity)
-constexpr int S = 64;        // slots of the staged face rings (global inputs)
-constexpr int SI = 4;        // slots of the rings between compute warps
-constexpr int AHEAD = 4;     // chunks the staging warp may run ahead
+constexpr int R = 4;          // rows per warp (registers)
+constexpr int W = 8;          // compute warps per CTA
+constexpr int WR = R * W;     // rows per CTA
+constexpr int U = 8;          // steps per block (the unrolled loop body), a multiple of 2R
+constexpr int SI = 32;        // depth of the rings into each warp (CTA-time entries), multiple of U
+constexpr int SF = 64;        // depth of the staged axis-1 face ring, multiple of U
+constexpr int F1S = WR + 4;   // ints per staged axis-1 face row: [3] row -1, [4 + rho] row rho
 constexpr int THREADS = 32 * (W + 1);  // compute warps + one staging warp
-constexpr int MAXA = 24;     // largest alphabet (replicated pair table)
-constexpr int MAXRHO2 = 4096;  // largest axis-2 extent (staged codes)
-constexpr int EXTRA = 0;     // sweep steps past the last position
-constexpr int CODEPAD = 64;  // axis-2 code staging pad on both sides
-// lockstep steps of one column: sweep TS = rho2 + R + 31 + EXTRA per warp, warps
-// lagging R steps each, rounded up to whole chunks
-__host__ __device__ constexpr int nsteps(int rho2) {
-    return ((rho2 + R + 31 + EXTRA + (W - 1) * R) + CH - 1) / CH * CH;
-}
-__host__ __device__ constexpr int face0_rows(int rho2) { return nsteps(rho2) + CH; }
-__host__ __device__ constexpr int face1_rows(int rho2) { return nsteps(rho2) + WR + CH; }
-// Traceback bytes of the column kernel are stored column-blocked and skewed:
-// column (A, B) owns sweep(rho2) * W * 32 * R bytes, and the move of cell
-// (x0 = A*WR + w*R + r, x1 = 32B + l, x2) sits at ((t*W + w)*32 + l)*R + r with
-// t = x2 + l + r, the warp step that computes it; so each warp step stores one
-// contiguous run of 32 lanes x R bytes.
-__host__ __device__ constexpr int sweep(int rho2) { return rho2 + R + 31 + EXTRA; }
-__host__ __device__ constexpr int64_t tb_col_bytes(int rho2) { return (int64_t)sweep(rho2) * W * 32 * R; }
-// faces hold (value, epoch tag) pairs: 2 ints per entry
-constexpr int F0W = 32 * 2;  // ints per axis-0 face row
-constexpr int F1W = WR * 2;  // ints per axis-1 face row
+constexpr int MAXA = 24;      // largest alphabet (replicated pair table)
+constexpr int MAXRHO2 = 4096; // largest axis-2 extent (staged codes)
+constexpr int CODEPAD = 96;   // axis-2 code staging pad on both sides
+constexpr int kSentinelPair = -(1 << 27);  // pair score of a move into x2 <= 0 (no residue)
+static_assert(U % (2 * R) == 0 && SI % U == 0 && SF % U == 0 && WR == 32, "column geometry");
+// CTA-time steps of one column: the last cell x2 = rho2 - 1 of lane 31, row
+// WR - 1 is computed at T = rho2 + WR + 29; rounded up to whole blocks. A column
+// runs T = -U .. nsteps - 1: the first block only fills the pipeline (its cells
+// lie at x2 < 0) so that time 0 starts with every candidate prepared.
+__host__ __device__ constexpr int nsteps(int rho2) { return (rho2 + WR + 30 + U - 1) / U * U; }
+// Faces between columns hold (value, tag) pairs, one 8-byte entry each, stored
+// from T = -U on (row T + U):
+//   F0[T][l]    row WR - 1 of the column at CTA time T, lane l (read by the column below)
+//   F1[T][rho]  lane 31 of the column at CTA time T, row rho (read by the columns to the
+//               right and, for rho = WR - 1, diagonally below-right)
+constexpr int F0W = 32 * 2;   // ints per F0 row
+constexpr int F1W = WR * 2;   // ints per F1 row
+__host__ __device__ constexpr int face0_rows(int rho2) { return nsteps(rho2) + U; }
+__host__ __device__ constexpr int face1_rows(int rho2) { return nsteps(rho2) + U; }
+// Traceback bytes are stored column-blocked and skewed: column (A, B) owns
+// (nsteps(rho2) + U) * W * 32 * R bytes, and the move of cell (x0 = A*WR + w*R + r,
+// x1 = 32B + l, x2) sits at (((T + U)*W + w)*32 + l)*R + r with
+// T = x2 + l + w*R + r, so each warp step stores one contiguous run of 32 lanes x
+// R bytes.
+__host__ __device__ constexpr int64_t tb_col_bytes(int rho2) { return (int64_t)(nsteps(rho2) + U) * W * 32 * R; }
 }  // namespace c3
 
 // Traceback box edge D per k (the box [x-D, x] is staged in shared memory; rows

@@ -10,13 +10,11 @@
 
 namespace msadp {
 
-// The k = 3 column kernel handles alphabets up to c3::MAXA, a last axis up to
-// c3::MAXRHO2, and keeps per-row traceback offsets in 32 bits.
+// The k = 3 column kernel handles alphabets up to c3::MAXA and a last axis up to
+// c3::MAXRHO2 (both staged in shared memory).
 static bool col3_fits(int k, const int32_t *lens, int A) {
     if (k != 3 || A > c3::MAXA) return false;
-    const int64_t rho2 = (int64_t)lens[2] + 1;
-    const int64_t row = (rho2 + kTbRowAlign - 1) / kTbRowAlign * kTbRowAlign;
-    return rho2 <= c3::MAXRHO2 && ((int64_t)lens[1] + 1) * row * c3::R < (1LL << 31);
+    return (int64_t)lens[2] + 1 <= c3::MAXRHO2;
 }
 
 int choose_kernel(int k, const int32_t *lens, int A, int requested) {
@@ -131,8 +129,8 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
 
     if (hp.kernel == kKernelCol3) {
         // faces between columns and the column order: a column (a, b) can start
-        // about a*(WR + CH) + b*(32 + CH) lockstep steps after the first, so
-        // tickets follow that estimate (every producer gets a smaller ticket)
+        // about a*(WR + U) + b*(32 + U) CTA-time steps after the first, so tickets
+        // follow that estimate (every producer gets a smaller ticket)
         const int rho2 = hp.rho[2];
         hp.face0_rows = c3::face0_rows(rho2);
         hp.face1_rows = c3::face1_rows(rho2);
@@ -145,7 +143,7 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
         std::vector<std::pair<int64_t, int64_t>> key(nt);
         for (int64_t t = 0; t < nt; ++t) {
             const int64_t a = t / hp.G[1], b = t % hp.G[1];
-            key[t] = {a * (c3::WR + c3::CH) + b * (32 + c3::CH), t};
+            key[t] = {a * (c3::WR + c3::U) + b * (32 + c3::U), t};
         }
         std::sort(key.begin(), key.end());
         hp.order.resize(nt);
