@@ -33,6 +33,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 import inputs  # noqa: E402
 
 METRIC = "DP cells/s"
@@ -149,6 +151,130 @@ def measured_traffic(workload: str, kernel: str):
     if not rec or rec.get("source_digest") != kernel_source_digest():
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+def serving_requests(n: int):
+    """The seeded serving stream as ready-to-submit C-ABI request structs."""
+    import ctypes
+
+    from paper_2311_17530_gb300 import msadp
+    out = []
+    for i in range(n):
+        p = inputs.serving_request(i)
+        enc = [s.encode() for s in p.seqs]
+        keep = (enc, (ctypes.c_char_p * p.k)(*enc), msadp._i32(p.lens), p.alphabet.encode(), msadp._table(p.subst))
+        req = msadp.Request(p.k, keep[1], keep[2], keep[3], keep[4], int(p.gap))
+        out.append((p, req, keep))
+    return out
+
+
+def serve_run(reqs, arrivals=None, collect=False, timeout_s=120.0):
+    """Submit every request (at its Poisson arrival time, or all at once) through
+    msa_submit; a second thread takes completions from msa_wait_any and releases
+    them with msa_poll. Latency = completion seen - msa_submit returned."""
+    import ctypes
+    import threading
+
+    from paper_2311_17530_gb300 import msadp
+    L = msadp.library()
+    n = len(reqs)
+    submit_t = [0.0] * n
+    done_t = [0.0] * n
+    index = {}
+    results = [None] * n if collect else None
+    lock = threading.Lock()
+    failure = []
+
+    def completer():
+        got = 0
+        deadline = time.perf_counter() + timeout_s
+        h = ctypes.c_uint64(0)
+        score = ctypes.c_int32(0)
+        while got < n:
+            rc = L.msa_wait_any(100000, ctypes.byref(h))
+            t = time.perf_counter()
+            if rc == msadp.MSA_PENDING:
+                if t > deadline:
+                    failure.append("serving did not finish in time")
+                    return
+                continue
+            with lock:
+                i = index[h.value]
+            done_t[i] = t
+            p = reqs[i][0]
+            stride = sum(p.lens) + 1
+            buf = ctypes.create_string_buffer(p.k * stride)
+            rc = L.msa_poll(h, ctypes.byref(score), buf)
+            if rc != 0:
+                failure.append(f"request {i}: status {rc} {msadp.last_error()}")
+            elif collect:
+                results[i] = (score.value, buf.raw)
+            got += 1
+
+    th = threading.Thread(target=completer)
+    th.start()
+    t0 = time.perf_counter()
+    h = ctypes.c_uint64(0)
+    for i, (p, req, _) in enumerate(reqs):
+        if arrivals is not None:
+            target = t0 + float(arrivals[i])
+            while True:
+                now = time.perf_counter()
+                if now >= target:
+                    break
+                if target - now > 0.0006:
+                    time.sleep(target - now - 0.0004)
+        with lock:
+            rc = L.msa_submit(ctypes.byref(req), ctypes.byref(h))
+            submit_t[i] = time.perf_counter()
+            if rc != 0:
+                raise SystemExit(f"msa_submit: {msadp.last_error()}")
+            index[h.value] = i
+    th.join()
+    if failure:
+        raise SystemExit(failure[0])
+    lat = np.array([done_t[i] - submit_t[i] for i in range(n)]) * 1e3
+    span = max(done_t) - min(submit_t)
+    cells = sum(r[0].cells for r in reqs)
+    return {"alignments_per_s": n / span, "cells_per_s": cells / span, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean())}, results
+
+
+def run_serving(n: int):
+    """Served alignments/s and p50/p99 latency: plain one-at-a-time launches
+    against continuous batching with graph-captured persistent launches, closed
+    loop and under Poisson arrivals at multiples of the plain saturation rate."""
+    from paper_2311_17530_gb300 import msadp
+    reqs = serving_requests(n)
+
+    def mode(batched):
+        msadp.msa_config("batching", 1 if batched else 0)
+        msadp.msa_config("use_graphs", 1)
+
+    mode(True)
+    serve_run(reqs[:128])  # warm-up: arena, kernels, graphs
+    mode(False)
+    serve_run(reqs[:16])
+    plain, res_plain = serve_run(reqs, collect=True)
+    mode(True)
+    batched, res_batched = serve_run(reqs, collect=True)
+    if res_plain != res_batched:
+        raise SystemExit("batched results differ from one-at-a-time results")
+    rate = plain["alignments_per_s"]
+    sweep = []
+    for x in (0.25, 0.5, 1.0, 2.0, 4.0):
+        arr = inputs.serving_arrivals(n, x * rate)
+        for batched_mode in (True, False):
+            mode(batched_mode)
+            r, _ = serve_run(reqs, arrivals=arr)
+            sweep.append({"mode": "batched+graphs" if batched_mode else "plain", "rate_x_plain_saturation": x,
+                          "offered_per_s": x * rate, **r})
+    mode(True)
+    ks = [r[0].k for r in reqs]
+    return {"requests": n, "stream": "seeded (request i: seed 5e6+i), k=2/3/4 at "
+                                     f"{ks.count(2)}/{ks.count(3)}/{ks.count(4)}",
+            "results_identical": True, "plain_closed_loop": plain, "batched_closed_loop": batched,
+            "speedup_closed_loop": batched["alignments_per_s"] / plain["alignments_per_s"], "poisson_sweep": sweep}
 
 
 def dist_setup():
@@ -283,6 +409,10 @@ def run_gb300(args, rank, world, local):
                 "traceback_ms": tb_ms,
                 "peak_basis": f"{sms} SMs x {INT32_LANES_PER_SM} INT32 lanes x {sm_max_mhz():.0f} MHz"}
 
+    serving = None
+    if world == 1 and not args.no_serving:
+        serving = run_serving(args.serve_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         q, dt = time_oracle(p, args.cpu_cells)
@@ -299,7 +429,7 @@ def run_gb300(args, rank, world, local):
                        "l2": "working set > L2 (no flush)", "parallelism": f"replicas{world}",
                        "score": score, "score_matches_oracle": checked},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 3 * args.steps, "clocks": clk,
+            "gpu_launches": 3 * args.steps, "clocks": clk, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     plan.close()
@@ -317,6 +447,8 @@ def main():
     ap.add_argument("--workload", default="k3_protein", choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving stream")
     ap.add_argument("--cpu-cells", type=float, default=1.2e8, help="cells of the cpu_baseline sample")
     ap.add_argument("--ref-cells", type=float, default=5e7, help="cells per step of --impl reference")
     args = ap.parse_args()

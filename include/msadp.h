@@ -235,6 +235,15 @@ int msa_cancel(uint64_t handle);
 /* Block until every submitted request has finished (results stay pollable). */
 int msa_drain(void);
 
+/*
+ * Completion queue: wait up to timeout_us microseconds for a request to finish
+ * and return MSA_OK with its handle in *out_handle (every finished request is
+ * reported once, in completion order; handles already released by msa_poll or
+ * msa_cancel are skipped), or MSA_PENDING when none finished in time. The
+ * reported handle is then read with msa_poll. Thread-safe.
+ */
+int msa_wait_any(int64_t timeout_us, uint64_t *out_handle);
+
 /* ------------------------------------------------------------------------ */
 /* Host-only planner queries (no CUDA calls; usable without a GPU).         */
 /* ------------------------------------------------------------------------ */

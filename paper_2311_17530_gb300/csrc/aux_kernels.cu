@@ -301,10 +301,16 @@ __global__ void __launch_bounds__(32) traceback_kernel(const ProblemDesc *probs,
     }
 }
 
+static cudaError_t traceback_attributes() {
+    static DeviceOnce once;  // attribute set once per device, never inside a stream capture
+    return once.run([] {
+        return cudaFuncSetAttribute(traceback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTracebackSmem);
+    });
+}
+
 cudaError_t launch_traceback(const ProblemDesc *d_probs, int nprob, const int32_t *err,
                              const IODesc *io_array, IODesc io_single, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(traceback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kTracebackSmem);
+    cudaError_t e = traceback_attributes();
     if (e != cudaSuccess) return e;
     traceback_kernel<<<nprob, 32, kTracebackSmem, s>>>(d_probs, err, io_array, io_single);
     return cudaGetLastError();
@@ -320,5 +326,17 @@ cudaError_t launch_fill_tiles(int k, const LaunchDesc &L, int grid, cudaStream_t
 }
 
 int fill_tiles_ctas_per_sm(int k) { return k <= 4 ? fill_tiles_ctas_lo(k) : fill_tiles_ctas_hi(k); }
+
+cudaError_t col3_attributes();
+
+// Every kernel attribute the launch wrappers need on the current device, so that
+// a later stream capture contains launches only.
+cudaError_t prepare_kernel_attributes() {
+    cudaError_t e = traceback_attributes();
+    if (e == cudaSuccess) e = col3_attributes();
+    for (int k = 2; k <= MSA_MAX_K && e == cudaSuccess; ++k)
+        if (fill_tiles_ctas_per_sm(k) <= 0) e = cudaErrorInvalidValue;
+    return e;
+}
 
 }  // namespace msadp

@@ -504,10 +504,17 @@ int col3_smem_bytes(int alphabet_size) {
            (c3::MAXRHO2 + 2 * c3::CODEPAD + 16) * 2 + 16;
 }
 
+// The attribute allows the largest alphabet's layout; set once per device.
+cudaError_t col3_attributes() {
+    static DeviceOnce once;
+    return once.run([] {
+        return cudaFuncSetAttribute(fill_col3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    col3_smem_bytes(c3::MAXA));
+    });
+}
+
 int fill_col3_ctas_per_sm(int smem) {
-    if (cudaFuncSetAttribute(fill_col3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
-        cudaSuccess)
-        return 0;
+    if (col3_attributes() != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fill_col3_kernel, c3::THREADS, smem) != cudaSuccess)
         return 0;
@@ -515,8 +522,9 @@ int fill_col3_ctas_per_sm(int smem) {
 }
 
 cudaError_t launch_fill_col3(const LaunchDesc &L, int grid, int smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(fill_col3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = col3_attributes();
     if (e != cudaSuccess) return e;
+    if (smem > col3_smem_bytes(c3::MAXA)) return cudaErrorInvalidValue;
     fill_col3_kernel<<<grid, c3::THREADS, smem, s>>>(L);
     return cudaGetLastError();
 }

@@ -294,11 +294,21 @@ fill_tiles_kernel(const LaunchDesc L) {
     }
 }
 
+// Shared-memory attribute of fill_tiles_kernel<K>, set once per device (so that
+// no launch inside a stream capture makes the call).
+template <int K>
+cudaError_t tiles_attributes_k() {
+    static DeviceOnce once;
+    return once.run([] {
+        return cudaFuncSetAttribute(fill_tiles_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tiles_smem_bytes<K>());
+    });
+}
+
 template <int K>
 cudaError_t launch_tiles_k(const LaunchDesc &L, int grid, cudaStream_t s) {
     constexpr int smem = tiles_smem_bytes<K>();
-    cudaError_t e = cudaFuncSetAttribute(fill_tiles_kernel<K>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = tiles_attributes_k<K>();
     if (e != cudaSuccess) return e;
     fill_tiles_kernel<K><<<grid, TilesCfg<K>::WARPS * 32, smem, s>>>(L);
     return cudaGetLastError();
@@ -307,9 +317,7 @@ cudaError_t launch_tiles_k(const LaunchDesc &L, int grid, cudaStream_t s) {
 template <int K>
 int tiles_ctas_k() {
     constexpr int smem = tiles_smem_bytes<K>();
-    if (cudaFuncSetAttribute(fill_tiles_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem) != cudaSuccess)
-        return 0;
+    if (tiles_attributes_k<K>() != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fill_tiles_kernel<K>,
                                                       TilesCfg<K>::WARPS * 32, smem) != cudaSuccess)

@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "../../include/msadp.h"
 
 namespace msadp {
@@ -154,12 +157,38 @@ constexpr int kTracebackSmem = 72 * 1024;
 // The traceback tensor's last axis is padded to this many bytes (16-byte rows).
 constexpr int kTbRowAlign = 16;
 
+// Runs a host action once per device (the current device when called), e.g. a
+// kernel attribute, so that launch wrappers make no such call while a stream is
+// being captured into a graph after the first use.
+class DeviceOnce {
+  public:
+    template <class F>
+    cudaError_t run(F f) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return f();
+        const unsigned long long bit = 1ull << dev;
+        if (done_.load(std::memory_order_acquire) & bit) return cudaSuccess;
+        std::lock_guard<std::mutex> g(mu_);
+        if (done_.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+        e = f();
+        if (e == cudaSuccess) done_.fetch_or(bit, std::memory_order_release);
+        return e;
+    }
+
+  private:
+    std::atomic<unsigned long long> done_{0};
+    std::mutex mu_;
+};
+
 // Kernel entry points (host wrappers), defined in the .cu files.
 // A kernel reads its per-problem IODesc from io_array[p] when io_array is set,
 // else from io_single (single-problem executions pass it by value).
 cudaError_t launch_encode(const ProblemDesc *d_probs, int nprob, int max_ncode,
                           const IODesc *io_array, IODesc io_single, cudaStream_t s);
 cudaError_t launch_fill_tiles(int k, const LaunchDesc &L, int grid, cudaStream_t s);
+cudaError_t prepare_kernel_attributes();
 int fill_tiles_ctas_per_sm(int k);
 cudaError_t launch_fill_col3(const LaunchDesc &L, int grid, int smem, cudaStream_t s);
 int fill_col3_ctas_per_sm(int smem);

@@ -31,7 +31,7 @@ _NAMES = {MSA_EINVAL: "MSA_EINVAL", MSA_ETOOBIG: "MSA_ETOOBIG", MSA_ENOMEM: "MSA
 EXPORTED = ["msa_align", "msa_last_error", "msa_set_stream", "msa_config", "msa_plan_create",
             "msa_plan_execute", "msa_plan_get_info", "msa_plan_destroy", "msa_submit", "msa_poll",
             "msa_cancel", "msa_drain", "msa_wave_sizes", "msa_tile_shape", "msa_version",
-            "msa_plan_read_tb", "msa_plan_timings", "msa_align_noalloc"]
+            "msa_plan_read_tb", "msa_plan_timings", "msa_align_noalloc", "msa_wait_any"]
 
 
 class MsaError(RuntimeError):
@@ -86,6 +86,7 @@ def library() -> ctypes.CDLL:
     L.msa_submit.argtypes = [ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     L.msa_poll.argtypes = [ctypes.c_uint64, i32p, ctypes.c_char_p]
     L.msa_cancel.argtypes = [ctypes.c_uint64]
+    L.msa_wait_any.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
     L.msa_wave_sizes.argtypes = [ctypes.c_int, i32p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, i32p]
     L.msa_tile_shape.argtypes = [ctypes.c_int, i32p, i32p, i32p]
     _lib = L
@@ -264,6 +265,16 @@ def msa_cancel(handle: int) -> None:
 
 def msa_drain() -> None:
     _check(library().msa_drain())
+
+
+def msa_wait_any(timeout_us: int) -> Optional[int]:
+    """Handle of the next finished request (completion order), or None after the timeout."""
+    h = ctypes.c_uint64(0)
+    rc = library().msa_wait_any(int(timeout_us), ctypes.byref(h))
+    if rc == MSA_PENDING:
+        return None
+    _check(rc)
+    return int(h.value)
 
 
 # ---------------------------------------------------------------------------
