@@ -251,6 +251,9 @@ def run_serving(n: int):
         msadp.msa_config("batching", 1 if batched else 0)
         msadp.msa_config("use_graphs", 1)
 
+    # tile shapes per k tuned on the stream's median shapes (protein alphabet)
+    tuned = {k: msadp.msa_autotune(lens, 20, repeats=2)["best"]
+             for k, lens in ((2, [1100, 1100]), (3, [170, 170, 170]), (4, [50, 50, 50, 50]))}
     mode(True)
     serve_run(reqs[:128])  # warm-up: arena, kernels, graphs
     mode(False)
@@ -273,7 +276,7 @@ def run_serving(n: int):
     ks = [r[0].k for r in reqs]
     return {"requests": n, "stream": "seeded (request i: seed 5e6+i), k=2/3/4 at "
                                      f"{ks.count(2)}/{ks.count(3)}/{ks.count(4)}",
-            "results_identical": True, "plain_closed_loop": plain, "batched_closed_loop": batched,
+            "results_identical": True, "autotuned": tuned, "plain_closed_loop": plain, "batched_closed_loop": batched,
             "speedup_closed_loop": batched["alignments_per_s"] / plain["alignments_per_s"], "poisson_sweep": sweep}
 
 
@@ -326,6 +329,8 @@ def run_gb300(args, rank, world, local):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     p = inputs.WORKLOADS[args.workload]()
     total_len = sum(p.lens)
+    # the autotuner picks the tile shape (and for k = 3 the kernel) for this shape
+    tuning = None if args.no_autotune else msadp.msa_autotune(p.lens, len(p.alphabet), repeats=2)
     plan = msadp.Plan(p.k, p.lens, p.alphabet)
     info = plan.info()
     d_res, d_sub = msadp.device_inputs(p, dev)
@@ -427,7 +432,7 @@ def run_gb300(args, rank, world, local):
             "config": {"workload": p.name, "k": p.k, "lens": p.lens, "cells": p.cells,
                        "tiles": int(info.tiles), "fill_kernel": kernel,
                        "l2": "working set > L2 (no flush)", "parallelism": f"replicas{world}",
-                       "score": score, "score_matches_oracle": checked},
+                       "score": score, "score_matches_oracle": checked, "autotune": tuning},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": 3 * args.steps, "clocks": clk, "serving": serving,
         }
@@ -448,6 +453,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
     ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving stream")
     ap.add_argument("--cpu-cells", type=float, default=1.2e8, help="cells of the cpu_baseline sample")
     ap.add_argument("--ref-cells", type=float, default=5e7, help="cells per step of --impl reference")

@@ -260,6 +260,42 @@ int msa_wave_sizes(int k, const int32_t *grid, int64_t *out_sizes, int32_t max_w
 /* The tile extents and tile grid the planner uses for these lengths. */
 int msa_tile_shape(int k, const int32_t *lens, int32_t *out_extent, int32_t *out_grid);
 
+/*
+ * Tile edge of the generic kernel for k (the paper's partition size S, section
+ * 3.2): the tile spans `edge` cells on every axis (k = 2: edge x 2*edge). Only
+ * compiled edges are accepted (k=2: 16 32 64; k=3: 8 12 16; k=4: 4 6 8; k=5: 3 4
+ * 5; k=6: 2 3 4; k=7: 2 3; k=8: 2); 0 restores the default (for k = 3 also the
+ * automatic choice of the column kernel where it fits). Later plans and serving
+ * batches use the setting. Host-only, thread-safe.
+ */
+int msa_set_tile_edge(int k, int32_t edge);
+int msa_get_tile_edge(int k, int32_t *out_edge);
+
+/* ------------------------------------------------------------------------ */
+/* Autotuner (no counterpart in the paper, which fixes S by hand).          */
+/* ------------------------------------------------------------------------ */
+
+#define MSA_MAX_TUNING_CANDIDATES 8
+
+typedef struct msa_tuning {
+    int32_t k;
+    int32_t ncand;                                   /* candidates timed */
+    int32_t cand_kernel[MSA_MAX_TUNING_CANDIDATES];  /* 1 generic tiles, 2 k=3 column kernel */
+    int32_t cand_edge[MSA_MAX_TUNING_CANDIDATES];    /* tile edge (0 for the column kernel) */
+    float cand_ms[MSA_MAX_TUNING_CANDIDATES];        /* mean ms of one execution (encode+fill+traceback) */
+    int32_t best;                                    /* index of the chosen candidate */
+} msa_tuning;
+
+/*
+ * Time every compiled tile edge for k (and, for k = 3, the column kernel) on a
+ * synthetic problem with these lengths over an alphabet of alphabet_size
+ * letters: one warm-up and `repeats` executions each, on the library stream. The
+ * fastest becomes the choice for k (msa_set_tile_edge, and for k = 3 whether the
+ * automatic kernel choice takes the column kernel). Allocates device memory;
+ * synchronous.
+ */
+int msa_autotune(int k, const int32_t *lens, int alphabet_size, int32_t repeats, msa_tuning *out);
+
 /* Library version string. */
 const char *msa_version(void);
 

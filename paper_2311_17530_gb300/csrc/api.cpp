@@ -2,6 +2,7 @@
 // the host-only planner queries.
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -113,15 +114,22 @@ int device_sm_count() {
     return sms;
 }
 
-int persistent_grid(int k, int kernel, int64_t units, int A) {
+int persistent_grid(int k, int kernel, int64_t units, int A, int edge) {
+    // resident CTAs per SM, cached per (kernel, k, alphabet size or tile edge)
+    static std::mutex mu;
     static int cache[3][MSA_MAX_K + 1][MSA_MAX_ALPHABET + 1] = {};
-    int &c = cache[kernel][k][kernel == kKernelCol3 ? A : 0];
-    if (!c) {
-        c = kernel == kKernelCol3 ? fill_col3_ctas_per_sm(col3_smem_bytes(A)) : fill_tiles_ctas_per_sm(k);
-        if (c <= 0) c = 1;
+    int c;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        int &slot = cache[kernel][k][kernel == kKernelCol3 ? A : (edge & 31)];
+        if (!slot) {
+            slot = kernel == kKernelCol3 ? fill_col3_ctas_per_sm(col3_smem_bytes(A)) : fill_tiles_ctas_per_sm(k, edge);
+            if (slot <= 0) slot = 1;
+        }
+        c = slot;
     }
     // the tile kernel takes one unit per warp, the column kernel one per CTA
-    const int per_cta = kernel == kKernelCol3 ? 1 : tiles_warps_per_cta(k);
+    const int per_cta = kernel == kKernelCol3 ? 1 : std::max(1, fill_tiles_warps_per_cta(k, edge));
     int64_t need = (units + per_cta - 1) / per_cta;
     int64_t g = (int64_t)c * device_sm_count();
     if (need < g) g = need;
@@ -216,7 +224,7 @@ cudaError_t clear_faces(const HostPlan &hp, const PlanPointers &pp, cudaStream_t
 
 int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t s) {
     cudaError_t e = hp.kernel == kKernelCol3 ? launch_fill_col3(L, grid, col3_smem_bytes(hp.A), s)
-                                             : launch_fill_tiles(hp.k, L, grid, s);
+                                             : launch_fill_tiles(hp.k, hp.edge, L, grid, s);
     return e == cudaSuccess ? MSA_OK : cuda_error(e, "fill kernel launch");
 }
 
@@ -282,21 +290,29 @@ int msa_config(const char *key, int64_t value) {
 }
 
 int msa_plan_create(int k, const int32_t *lens, const char *alphabet, msa_plan **out_plan) {
+    int kernel_choice;
+    {
+        std::lock_guard<std::mutex> g(settings_mutex());
+        kernel_choice = (int)settings().fill_kernel;
+    }
+    return msadp::plan_create(k, lens, alphabet, kernel_choice, -1, out_plan);
+}
+
+}  // extern "C"
+
+namespace msadp {
+
+int plan_create(int k, const int32_t *lens, const char *alphabet, int kernel_choice, int edge, msa_plan **out_plan) {
     if (!out_plan) return set_error(MSA_EINVAL, "out_plan is NULL");
     *out_plan = nullptr;
     uint8_t amap[256];
     int rc = validate_alphabet(alphabet, amap);
     if (rc) return rc;
     const int A = (int)strlen(alphabet);
-    int kernel_choice;
-    {
-        std::lock_guard<std::mutex> g(settings_mutex());
-        kernel_choice = (int)settings().fill_kernel;
-    }
     msa_plan *p = new (std::nothrow) msa_plan();
     if (!p) return set_error(MSA_ENOMEM, "host allocation failed");
     std::string err;
-    rc = make_plan(k, lens, A, kernel_choice, p->hp, err);
+    rc = make_plan(k, lens, A, kernel_choice, p->hp, err, edge);
     if (rc) {
         delete p;
         return set_error(rc, "%s", err.c_str());
@@ -326,10 +342,14 @@ int msa_plan_create(int k, const int32_t *lens, const char *alphabet, msa_plan *
         delete p;
         return cuda_error(e, "plan upload");
     }
-    p->grid = persistent_grid(k, p->hp.kernel, p->hp.ntiles, A);
+    p->grid = persistent_grid(k, p->hp.kernel, p->hp.ntiles, A, p->hp.edge);
     *out_plan = p;
     return MSA_OK;
 }
+
+}  // namespace msadp
+
+extern "C" {
 
 int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_subst, int32_t gap,
                      msa_device_result *d_result, uint8_t *d_masks, void *stream) {

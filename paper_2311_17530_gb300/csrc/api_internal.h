@@ -43,7 +43,6 @@ struct PlanPointers {
     int32_t *aux = nullptr;
 };
 
-constexpr int tiles_warps_per_cta(int k) { return k <= 5 ? 8 : 4; }
 int col3_warps_per_cta();
 
 int set_error(int code, const char *fmt, ...);
@@ -55,7 +54,9 @@ int validate_alphabet(const char *alphabet, uint8_t amap[256]);
 int validate_request(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
                      const int32_t *subst, uint8_t amap[256]);
 int status_error(int status);
-int persistent_grid(int k, int kernel, int64_t units, int A);
+int persistent_grid(int k, int kernel, int64_t units, int A, int edge);
+// msa_plan_create with an explicit kernel choice and tile edge (edge < 0: tuned).
+int plan_create(int k, const int32_t *lens, const char *alphabet, int kernel_choice, int edge, msa_plan **out_plan);
 size_t plan_layout(const HostPlan &hp, char *base, PlanPointers *pp, size_t *reset_bytes);
 void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_base, ProblemDesc &d);
 int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t s);

@@ -316,16 +316,57 @@ cudaError_t launch_traceback(const ProblemDesc *d_probs, int nprob, const int32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill_tiles_lo(int k, const LaunchDesc &L, int grid, cudaStream_t s);
-cudaError_t launch_fill_tiles_hi(int k, const LaunchDesc &L, int grid, cudaStream_t s);
-int fill_tiles_ctas_lo(int k);
-int fill_tiles_ctas_hi(int k);
+#define MSADP_TILES_K(k)                                                                      \
+    cudaError_t launch_fill_tiles_k##k(int edge, const LaunchDesc &L, int grid, cudaStream_t s); \
+    int fill_tiles_ctas_k##k(int edge);                                                          \
+    int fill_tiles_warps_k##k(int edge);
+MSADP_TILES_K(2)
+MSADP_TILES_K(3)
+MSADP_TILES_K(4)
+MSADP_TILES_K(5)
+MSADP_TILES_K(6)
+MSADP_TILES_K(7)
+MSADP_TILES_K(8)
+#undef MSADP_TILES_K
 
-cudaError_t launch_fill_tiles(int k, const LaunchDesc &L, int grid, cudaStream_t s) {
-    return k <= 4 ? launch_fill_tiles_lo(k, L, grid, s) : launch_fill_tiles_hi(k, L, grid, s);
+cudaError_t launch_fill_tiles(int k, int edge, const LaunchDesc &L, int grid, cudaStream_t s) {
+    switch (k) {
+        case 2: return launch_fill_tiles_k2(edge, L, grid, s);
+        case 3: return launch_fill_tiles_k3(edge, L, grid, s);
+        case 4: return launch_fill_tiles_k4(edge, L, grid, s);
+        case 5: return launch_fill_tiles_k5(edge, L, grid, s);
+        case 6: return launch_fill_tiles_k6(edge, L, grid, s);
+        case 7: return launch_fill_tiles_k7(edge, L, grid, s);
+        case 8: return launch_fill_tiles_k8(edge, L, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
-int fill_tiles_ctas_per_sm(int k) { return k <= 4 ? fill_tiles_ctas_lo(k) : fill_tiles_ctas_hi(k); }
+int fill_tiles_ctas_per_sm(int k, int edge) {
+    switch (k) {
+        case 2: return fill_tiles_ctas_k2(edge);
+        case 3: return fill_tiles_ctas_k3(edge);
+        case 4: return fill_tiles_ctas_k4(edge);
+        case 5: return fill_tiles_ctas_k5(edge);
+        case 6: return fill_tiles_ctas_k6(edge);
+        case 7: return fill_tiles_ctas_k7(edge);
+        case 8: return fill_tiles_ctas_k8(edge);
+        default: return 0;
+    }
+}
+
+int fill_tiles_warps_per_cta(int k, int edge) {
+    switch (k) {
+        case 2: return fill_tiles_warps_k2(edge);
+        case 3: return fill_tiles_warps_k3(edge);
+        case 4: return fill_tiles_warps_k4(edge);
+        case 5: return fill_tiles_warps_k5(edge);
+        case 6: return fill_tiles_warps_k6(edge);
+        case 7: return fill_tiles_warps_k7(edge);
+        case 8: return fill_tiles_warps_k8(edge);
+        default: return 0;
+    }
+}
 
 cudaError_t col3_attributes();
 
@@ -335,7 +376,9 @@ cudaError_t prepare_kernel_attributes() {
     cudaError_t e = traceback_attributes();
     if (e == cudaSuccess) e = col3_attributes();
     for (int k = 2; k <= MSA_MAX_K && e == cudaSuccess; ++k)
-        if (fill_tiles_ctas_per_sm(k) <= 0) e = cudaErrorInvalidValue;
+        for (int i = 0; i < kMaxTileEdges && e == cudaSuccess; ++i)
+            if (tile_edge_candidate(k, i) > 0 && fill_tiles_ctas_per_sm(k, tile_edge_candidate(k, i)) <= 0)
+                e = cudaErrorInvalidValue;
     return e;
 }
 

@@ -48,53 +48,53 @@ __device__ __forceinline__ bool wait_at_least(const int32_t *flag, int need, con
     return false;
 }
 
-// Geometry of the generic tile kernel (compile-time per k).
-__host__ __device__ constexpr int geo_sh(int K, int i) {  // halo'd tile stride
+// Geometry of the generic tile kernel (compile-time per k and tile edge E).
+__host__ __device__ constexpr int geo_sh(int K, int E, int i) {  // halo'd tile stride
     int s = 1;
-    for (int j = K - 1; j > i; --j) s *= tile_extent(K, j) + 1;
+    for (int j = K - 1; j > i; --j) s *= tile_ext(K, E, j) + 1;
     return s;
 }
-__host__ __device__ constexpr int geo_st(int K, int i) {  // interior tile stride
+__host__ __device__ constexpr int geo_st(int K, int E, int i) {  // interior tile stride
     int s = 1;
-    for (int j = K - 1; j > i; --j) s *= tile_extent(K, j);
+    for (int j = K - 1; j > i; --j) s *= tile_ext(K, E, j);
     return s;
 }
-__host__ __device__ constexpr int geo_volh(int K) { return geo_sh(K, -1); }
-__host__ __device__ constexpr int geo_vol(int K) { return geo_st(K, -1); }
-__host__ __device__ constexpr int geo_planes(int K) {
+__host__ __device__ constexpr int geo_volh(int K, int E) { return geo_sh(K, E, -1); }
+__host__ __device__ constexpr int geo_vol(int K, int E) { return geo_st(K, E, -1); }
+__host__ __device__ constexpr int geo_planes(int K, int E) {
     int s = 0;
-    for (int i = 0; i < K; ++i) s += tile_extent(K, i);
+    for (int i = 0; i < K; ++i) s += tile_ext(K, E, i);
     return s - K + 1;
 }
-__host__ __device__ constexpr int geo_codes(int K) {
+__host__ __device__ constexpr int geo_codes(int K, int E) {
     int s = 0;
-    for (int i = 0; i < K; ++i) s += tile_extent(K, i);
+    for (int i = 0; i < K; ++i) s += tile_ext(K, E, i);
     return s;
 }
-__host__ __device__ constexpr int geo_code_base(int K, int i) {
+__host__ __device__ constexpr int geo_code_base(int K, int E, int i) {
     int s = 0;
-    for (int j = 0; j < i; ++j) s += tile_extent(K, j);
+    for (int j = 0; j < i; ++j) s += tile_ext(K, E, j);
     return s;
 }
 // smem offset of the predecessor x - e_m relative to x
-__host__ __device__ constexpr int move_soff(int K, int m) {
+__host__ __device__ constexpr int move_soff(int K, int E, int m) {
     int s = 0;
     for (int i = 0; i < K; ++i)
-        if ((m >> i) & 1) s += geo_sh(K, i);
+        if ((m >> i) & 1) s += geo_sh(K, E, i);
     return s;
 }
 // cells of halo face f: first axis at local -1 is f
-__host__ __device__ constexpr int face_extent(int K, int f, int j) {
-    return j < f ? tile_extent(K, j) : (j == f ? 1 : tile_extent(K, j) + 1);
+__host__ __device__ constexpr int face_extent(int K, int E, int f, int j) {
+    return j < f ? tile_ext(K, E, j) : (j == f ? 1 : tile_ext(K, E, j) + 1);
 }
-__host__ __device__ constexpr int face_size(int K, int f) {
+__host__ __device__ constexpr int face_size(int K, int E, int f) {
     int s = 1;
-    for (int j = 0; j < K; ++j) s *= face_extent(K, f, j);
+    for (int j = 0; j < K; ++j) s *= face_extent(K, E, f, j);
     return s;
 }
-__host__ __device__ constexpr int face_stride(int K, int f, int i) {
+__host__ __device__ constexpr int face_stride(int K, int E, int f, int i) {
     int s = 1;
-    for (int j = K - 1; j > i; --j) s *= face_extent(K, f, j);
+    for (int j = K - 1; j > i; --j) s *= face_extent(K, E, f, j);
     return s;
 }
 __host__ __device__ constexpr int popc_c(int m) {

@@ -20,28 +20,40 @@
 
 namespace msadp {
 
-template <int K>
+// Shared memory: the intra-tile schedule (8 bytes per cell) and plane offsets
+// for the CTA, then per warp the halo'd score tile, the traceback tile and the
+// residue codes along each axis.
+template <int K, int E>
+__host__ __device__ constexpr int tiles_warp_bytes() {
+    return round_up(geo_volh(K, E) * 4, 16) + round_up(geo_vol(K, E), 16) + round_up(geo_codes(K, E), 16);
+}
+template <int K, int E>
+__host__ __device__ constexpr int tiles_cta_fixed_bytes() {
+    return round_up(geo_vol(K, E) * 8, 16) + round_up(geo_planes(K, E) + 1, 4) * 4 + round_up(geo_planes(K, E), 4) * 4;
+}
+// Warps per CTA: up to 8 (4 for k > 5), as many as fit in 200 KB of shared memory.
+template <int K, int E>
 struct TilesCfg {
-    static constexpr int WARPS = K <= 5 ? 8 : 4;
+    static constexpr int kMax = K <= 5 ? 8 : 4;
+    static constexpr int kFit = (200 * 1024 - tiles_cta_fixed_bytes<K, E>()) / tiles_warp_bytes<K, E>();
+    static constexpr int WARPS = kFit < 1 ? 1 : (kFit > kMax ? kMax : kFit);
+    static_assert(kFit >= 1, "tile does not fit in shared memory");
+    static_assert(geo_volh(K, E) < 65536 && geo_vol(K, E) < 65536, "schedule entries hold 16-bit offsets");
+    static_assert(E < (K <= 4 ? 256 : 16) && tile_ext(K, E, K - 1) < (K <= 4 ? 256 : 16),
+                  "packed local coordinates");
 };
 
-template <int K>
-__host__ __device__ constexpr int tiles_warp_bytes() {
-    return round_up(geo_volh(K) * 4, 16) + round_up(geo_vol(K), 16) + round_up(geo_codes(K), 16);
-}
-
-template <int K>
+template <int K, int E>
 __host__ __device__ constexpr int tiles_smem_bytes() {
-    return round_up(geo_vol(K) * 8, 16) + round_up(geo_planes(K) + 1, 4) * 4 +
-           round_up(geo_planes(K), 4) * 4 + TilesCfg<K>::WARPS * tiles_warp_bytes<K>();
+    return tiles_cta_fixed_bytes<K, E>() + TilesCfg<K, E>::WARPS * tiles_warp_bytes<K, E>();
 }
 
-template <int K>
-__global__ void __launch_bounds__(TilesCfg<K>::WARPS * 32)
+template <int K, int E>
+__global__ void __launch_bounds__(TilesCfg<K, E>::WARPS * 32)
 fill_tiles_kernel(const LaunchDesc L) {
-    constexpr int VOL = geo_vol(K);
-    constexpr int VOLH = geo_volh(K);
-    constexpr int PLANES = geo_planes(K);
+    constexpr int VOL = geo_vol(K, E);
+    constexpr int VOLH = geo_volh(K, E);
+    constexpr int PLANES = geo_planes(K, E);
     constexpr int NM = (1 << K) - 1;
     constexpr int CB = K <= 4 ? 8 : 4;  // bits per packed local coordinate
     constexpr unsigned CMASK = (1u << CB) - 1;
@@ -62,8 +74,8 @@ fill_tiles_kernel(const LaunchDesc L) {
         int s = 0, rem = i;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const int c = rem / geo_st(K, j);
-            rem -= c * geo_st(K, j);
+            const int c = rem / geo_st(K, E, j);
+            rem -= c * geo_st(K, E, j);
             s += c;
         }
         atomicAdd(&pcur[s], 1);
@@ -84,10 +96,10 @@ fill_tiles_kernel(const LaunchDesc L) {
         uint32_t pk = 0;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const int c = rem / geo_st(K, j);
-            rem -= c * geo_st(K, j);
+            const int c = rem / geo_st(K, E, j);
+            rem -= c * geo_st(K, E, j);
             s += c;
-            soff += (c + 1) * geo_sh(K, j);
+            soff += (c + 1) * geo_sh(K, E, j);
             pk |= (uint32_t)c << (CB * j);
         }
         const int pos = atomicAdd(&pcur[s], 1);
@@ -95,7 +107,7 @@ fill_tiles_kernel(const LaunchDesc L) {
     }
     __syncthreads();
 
-    int32_t *qs = reinterpret_cast<int32_t *>(wbase + warp * tiles_warp_bytes<K>());
+    int32_t *qs = reinterpret_cast<int32_t *>(wbase + warp * tiles_warp_bytes<K, E>());
     unsigned char *tbs = reinterpret_cast<unsigned char *>(qs) + round_up(VOLH * 4, 16);
     unsigned char *tcs = tbs + round_up(VOL, 16);
 
@@ -118,9 +130,9 @@ fill_tiles_kernel(const LaunchDesc L) {
             const int64_t gs = P.gstride[j];
             tco[j] = (int)(rem / gs);
             rem -= tco[j] * gs;
-            o[j] = tco[j] * tile_extent(K, j);
+            o[j] = tco[j] * tile_ext(K, E, j);
             const int rho = P.rho[j];
-            e[j] = min(tile_extent(K, j), rho - o[j]);
+            e[j] = min(tile_ext(K, E, j), rho - o[j]);
             corner = corner && (o[j] + e[j] == rho);
             origin = origin && (o[j] == 0);
             len[j] = P.len[j];
@@ -152,9 +164,9 @@ fill_tiles_kernel(const LaunchDesc L) {
             // residue x_j - 1 of sequence j).
 #pragma unroll
             for (int j = 0; j < K; ++j)
-                for (int c = lane; c < tile_extent(K, j); c += 32) {
+                for (int c = lane; c < tile_ext(K, E, j); c += 32) {
                     const int x = o[j] + c;
-                    tcs[geo_code_base(K, j) + c] =
+                    tcs[geo_code_base(K, E, j) + c] =
                         (x >= 1 && x <= len[j]) ? codes[cofs[j] + x - 1] : (uint8_t)0;
                 }
 
@@ -165,23 +177,23 @@ fill_tiles_kernel(const LaunchDesc L) {
             constexpr int HB = 8;
 #pragma unroll
             for (int f = 0; f < K; ++f) {
-                for (int i0 = 0; i0 < face_size(K, f); i0 += 32 * HB) {
+                for (int i0 = 0; i0 < face_size(K, E, f); i0 += 32 * HB) {
                     int val[HB], dst[HB];
 #pragma unroll
                     for (int u = 0; u < HB; ++u) {
                         const int i = i0 + 32 * u + lane;
                         int r = i, soff = 0;
-                        bool in = i < face_size(K, f), neg = false;
+                        bool in = i < face_size(K, E, f), neg = false;
                         int64_t g = 0;
 #pragma unroll
                         for (int j = 0; j < K; ++j) {
-                            const int fs = face_stride(K, f, j);
+                            const int fs = face_stride(K, E, f, j);
                             int cj = r / fs;
                             r -= cj * fs;
                             if (j >= f) cj -= 1;
                             in = in && (cj < e[j]);
                             neg = neg || (cj < 0 && o[j] == 0);
-                            soff += (cj + 1) * geo_sh(K, j);
+                            soff += (cj + 1) * geo_sh(K, E, j);
                             g += (int64_t)(o[j] + cj) * qstr[j];
                         }
                         dst[u] = in ? soff : -1;
@@ -219,7 +231,7 @@ fill_tiles_kernel(const LaunchDesc L) {
                     }
                     int a[K];
 #pragma unroll
-                    for (int j = 0; j < K; ++j) a[j] = tcs[geo_code_base(K, j) + c[j]];
+                    for (int j = 0; j < K; ++j) a[j] = tcs[geo_code_base(K, E, j) + c[j]];
                     int pv[K][K];
 #pragma unroll
                     for (int i = 0; i < K; ++i)
@@ -245,7 +257,7 @@ fill_tiles_kernel(const LaunchDesc L) {
                     int acc = kNeg;
 #pragma unroll
                     for (int m = 1; m <= NM; ++m) {
-                        const int pred = qs[soff - move_soff(K, m)];
+                        const int pred = qs[soff - move_soff(K, E, m)];
                         if (popc_c(m) == 1)
                             acc = max(acc, pred);
                         else
@@ -267,10 +279,10 @@ fill_tiles_kernel(const LaunchDesc L) {
                 int64_t gq = 0, gt = 0;
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
-                    const int cj = r / geo_st(K, j);
-                    r -= cj * geo_st(K, j);
+                    const int cj = r / geo_st(K, E, j);
+                    r -= cj * geo_st(K, E, j);
                     in = in && (cj < e[j]);
-                    soff += (cj + 1) * geo_sh(K, j);
+                    soff += (cj + 1) * geo_sh(K, E, j);
                     gq += (int64_t)(o[j] + cj) * qstr[j];
                     gt += (int64_t)(o[j] + cj) * tstr[j];
                 }
@@ -282,7 +294,7 @@ fill_tiles_kernel(const LaunchDesc L) {
             if (corner && lane == 0) {
                 int soff = 0;
 #pragma unroll
-                for (int j = 0; j < K; ++j) soff += e[j] * geo_sh(K, j);
+                for (int j = 0; j < K; ++j) soff += e[j] * geo_sh(K, E, j);
                 *P.qcorner = qs[soff];
             }
         }
@@ -294,35 +306,66 @@ fill_tiles_kernel(const LaunchDesc L) {
     }
 }
 
-// Shared-memory attribute of fill_tiles_kernel<K>, set once per device (so that
-// no launch inside a stream capture makes the call).
-template <int K>
-cudaError_t tiles_attributes_k() {
+// Shared-memory attribute of fill_tiles_kernel<K, E>, set once per device (so
+// that no launch inside a stream capture makes the call).
+template <int K, int E>
+cudaError_t tiles_attributes() {
     static DeviceOnce once;
     return once.run([] {
-        return cudaFuncSetAttribute(fill_tiles_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    tiles_smem_bytes<K>());
+        return cudaFuncSetAttribute(fill_tiles_kernel<K, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tiles_smem_bytes<K, E>());
     });
 }
 
-template <int K>
-cudaError_t launch_tiles_k(const LaunchDesc &L, int grid, cudaStream_t s) {
-    constexpr int smem = tiles_smem_bytes<K>();
-    cudaError_t e = tiles_attributes_k<K>();
+template <int K, int E>
+cudaError_t launch_tiles(const LaunchDesc &L, int grid, cudaStream_t s) {
+    constexpr int smem = tiles_smem_bytes<K, E>();
+    cudaError_t e = tiles_attributes<K, E>();
     if (e != cudaSuccess) return e;
-    fill_tiles_kernel<K><<<grid, TilesCfg<K>::WARPS * 32, smem, s>>>(L);
+    fill_tiles_kernel<K, E><<<grid, TilesCfg<K, E>::WARPS * 32, smem, s>>>(L);
     return cudaGetLastError();
 }
 
-template <int K>
-int tiles_ctas_k() {
-    constexpr int smem = tiles_smem_bytes<K>();
-    if (tiles_attributes_k<K>() != cudaSuccess) return 0;
+template <int K, int E>
+int tiles_ctas() {
+    constexpr int smem = tiles_smem_bytes<K, E>();
+    if (tiles_attributes<K, E>() != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fill_tiles_kernel<K>,
-                                                      TilesCfg<K>::WARPS * 32, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fill_tiles_kernel<K, E>, TilesCfg<K, E>::WARPS * 32,
+                                                      smem) != cudaSuccess)
         return 0;
     return n;
 }
+
+// Dispatch of one k over its candidate edges (instantiated in fill_tiles_k<k>.cu).
+template <int K>
+struct TilesK {
+    static constexpr int E0 = tile_edge_candidate(K, 0), E1 = tile_edge_candidate(K, 1),
+                         E2 = tile_edge_candidate(K, 2);
+    static cudaError_t launch(int edge, const LaunchDesc &L, int grid, cudaStream_t s) {
+        if (edge == E0) return launch_tiles<K, E0>(L, grid, s);
+        if constexpr (E1 > 0)
+            if (edge == E1) return launch_tiles<K, E1>(L, grid, s);
+        if constexpr (E2 > 0)
+            if (edge == E2) return launch_tiles<K, E2>(L, grid, s);
+        return cudaErrorInvalidValue;
+    }
+    static int ctas(int edge) {
+        if (edge == E0) return tiles_ctas<K, E0>();
+        if constexpr (E1 > 0)
+            if (edge == E1) return tiles_ctas<K, E1>();
+        if constexpr (E2 > 0)
+            if (edge == E2) return tiles_ctas<K, E2>();
+        return 0;
+    }
+    static int warps(int edge) {
+        if (edge == E0) return TilesCfg<K, E0>::WARPS;
+        if constexpr (E1 > 0)
+            if (edge == E1) return TilesCfg<K, E1>::WARPS;
+        if constexpr (E2 > 0)
+            if (edge == E2) return TilesCfg<K, E2>::WARPS;
+        return 0;
+    }
+};
 
 }  // namespace msadp

@@ -91,14 +91,28 @@ struct LaunchDesc {
     int32_t pad2;
 };
 
-// Tile extents of the generic kernel, per k (compile-time in the kernel).
-__host__ __device__ constexpr int tile_extent(int k, int i) {
-    return k == 2 ? (i == 0 ? 32 : 64)
-         : k == 3 ? 12
-         : k == 4 ? 6
-         : k == 5 ? 4
-         : k == 6 ? 3
-         : 2;
+// Tile shapes of the generic kernel. A shape is named by its edge E: the tile
+// spans E cells on every axis, except k = 2 where it spans E x 2E. Each k has a
+// few compiled shapes (the autotuner picks among them; kTileEdgeDefault is used
+// until it has); the kernel is instantiated per (k, E).
+__host__ __device__ constexpr int tile_ext(int k, int edge, int i) { return k == 2 && i == 1 ? 2 * edge : edge; }
+constexpr int kMaxTileEdges = 3;
+// candidate edges per k (0 = unused slot)
+__host__ __device__ constexpr int tile_edge_candidate(int k, int idx) {
+    return k == 2 ? (idx == 0 ? 16 : idx == 1 ? 32 : 64)
+         : k == 3 ? (idx == 0 ? 8 : idx == 1 ? 12 : 16)
+         : k == 4 ? (idx == 0 ? 4 : idx == 1 ? 6 : 8)
+         : k == 5 ? (idx == 0 ? 3 : idx == 1 ? 4 : 5)
+         : k == 6 ? (idx == 0 ? 2 : idx == 1 ? 3 : 4)
+         : k == 7 ? (idx == 0 ? 2 : idx == 1 ? 3 : 0)
+         : (idx == 0 ? 2 : 0);
+}
+__host__ __device__ constexpr int tile_edge_default(int k) {
+    return k == 2 ? 32 : k == 3 ? 12 : k == 4 ? 6 : k == 5 ? 4 : k == 6 ? 3 : 2;
+}
+__host__ __device__ constexpr bool tile_edge_valid(int k, int edge) {
+    return edge > 0 && (tile_edge_candidate(k, 0) == edge || tile_edge_candidate(k, 1) == edge ||
+                        tile_edge_candidate(k, 2) == edge);
 }
 
 // k = 3 column kernel geometry (shared by the planner and the kernel).
@@ -187,9 +201,10 @@ class DeviceOnce {
 // else from io_single (single-problem executions pass it by value).
 cudaError_t launch_encode(const ProblemDesc *d_probs, int nprob, int max_ncode,
                           const IODesc *io_array, IODesc io_single, cudaStream_t s);
-cudaError_t launch_fill_tiles(int k, const LaunchDesc &L, int grid, cudaStream_t s);
+cudaError_t launch_fill_tiles(int k, int edge, const LaunchDesc &L, int grid, cudaStream_t s);
 cudaError_t prepare_kernel_attributes();
-int fill_tiles_ctas_per_sm(int k);
+int fill_tiles_ctas_per_sm(int k, int edge);
+int fill_tiles_warps_per_cta(int k, int edge);
 cudaError_t launch_fill_col3(const LaunchDesc &L, int grid, int smem, cudaStream_t s);
 int fill_col3_ctas_per_sm(int smem);
 int col3_smem_bytes(int alphabet_size);

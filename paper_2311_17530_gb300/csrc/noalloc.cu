@@ -92,7 +92,8 @@ int noalloc_plan(int k, const int32_t *lens, int A, HostPlan &hp) {
     hp.len_sum = (int32_t)len_sum;
     hp.w_corner = (int32_t)w_corner;
     hp.pair_min_sum = (int32_t)pair_min;
-    tile_extents(k, lens, kKernelTiles, hp.E);
+    hp.edge = tile_edge_for(k);
+    tile_extents(k, lens, kKernelTiles, hp.edge, hp.E);
     int64_t nt = 1;
     int gsum = 0;
     for (int i = k - 1; i >= 0; --i) {
@@ -198,7 +199,7 @@ extern "C" int msa_align_noalloc(int k, const int32_t *lens, const char *alphabe
     L.spin_ns = spin_ms * 1000000LL;
     L.withhold = -1;
     L.nprob = 1;
-    e = launch_fill_tiles(k, L, persistent_grid(k, kKernelTiles, hp.ntiles, A), s);
+    e = launch_fill_tiles(k, hp.edge, L, persistent_grid(k, kKernelTiles, hp.ntiles, A, hp.edge), s);
     if (e != cudaSuccess) return cuda_error(e, "fill launch");
     e = launch_traceback(pp.prob, 1, L.err, nullptr, io, s);
     if (e != cudaSuccess) return cuda_error(e, "traceback launch");

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 namespace msadp {
 
@@ -17,20 +18,49 @@ static bool col3_fits(int k, const int32_t *lens, int A) {
     return (int64_t)lens[2] + 1 <= c3::MAXRHO2;
 }
 
+namespace {
+std::mutex g_tune_mu;
+int g_edge[MSA_MAX_K + 1] = {};  // 0: default edge
+bool g_k3_tiles = false;
+}  // namespace
+
+int tile_edge_for(int k) {
+    if (k < 2 || k > MSA_MAX_K) return 0;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    return g_edge[k] ? g_edge[k] : tile_edge_default(k);
+}
+
+int set_tile_edge(int k, int edge) {
+    if (k < 2 || k > MSA_MAX_K || (edge != 0 && !tile_edge_valid(k, edge))) return MSA_EINVAL;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_edge[k] = edge;
+    return MSA_OK;
+}
+
+bool prefer_tiles_k3() {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    return g_k3_tiles;
+}
+
+void set_prefer_tiles_k3(bool v) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_k3_tiles = v;
+}
+
 int choose_kernel(int k, const int32_t *lens, int A, int requested) {
     if (requested == kKernelTiles) return kKernelTiles;
-    if (col3_fits(k, lens, A)) return kKernelCol3;
+    if (col3_fits(k, lens, A) && (requested == kKernelCol3 || !prefer_tiles_k3())) return kKernelCol3;
     return kKernelTiles;
 }
 
-void tile_extents(int k, const int32_t *lens, int kernel, int32_t *E) {
+void tile_extents(int k, const int32_t *lens, int kernel, int edge, int32_t *E) {
     if (kernel == kKernelCol3) {
         E[0] = c3::WR;
         E[1] = 32;
         E[2] = lens[2] + 1;
         return;
     }
-    for (int i = 0; i < k; ++i) E[i] = tile_extent(k, i);
+    for (int i = 0; i < k; ++i) E[i] = tile_ext(k, edge, i);
 }
 
 void wave_sizes(int k, const int32_t *grid, std::vector<int64_t> &out) {
@@ -49,7 +79,7 @@ void wave_sizes(int k, const int32_t *grid, std::vector<int64_t> &out) {
 
 static int64_t round_up64(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
-int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err) {
+int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err, int edge) {
     char buf[256];
     if (k < 2 || k > MSA_MAX_K) {
         snprintf(buf, sizeof buf, "k=%d outside [2,%d]", k, MSA_MAX_K);
@@ -94,7 +124,15 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
     hp.w_corner = (int32_t)w_corner;
     hp.pair_min_sum = (int32_t)std::min<int64_t>(pair_min, (1LL << 30));
 
-    tile_extents(k, lens, hp.kernel, hp.E);
+    if (hp.kernel == kKernelTiles) {
+        hp.edge = edge < 0 ? tile_edge_for(k) : edge;
+        if (!tile_edge_valid(k, hp.edge)) {
+            snprintf(buf, sizeof buf, "tile edge %d is not compiled for k=%d", hp.edge, k);
+            err = buf;
+            return MSA_EINVAL;
+        }
+    }
+    tile_extents(k, lens, hp.kernel, hp.edge, hp.E);
     int64_t nt = 1;
     for (int i = k - 1; i >= 0; --i) {
         hp.G[i] = (hp.rho[i] + hp.E[i] - 1) / hp.E[i];

@@ -35,17 +35,28 @@ struct HostPlan {
     int64_t tbbytes = 0;               // row-major size
     int32_t tb_layout = 0;             // device layout: 0 row-major, 1 column-blocked
     int64_t tb_dev_bytes = 0;          // device size of the traceback tensor
+    int32_t edge = 0;              // tile edge of the generic kernel (tile_ext), 0 for the column kernel
     int32_t pair_min_sum = 0;
     int32_t w_corner = 0;
     int32_t len_sum = 0;
     std::vector<uint64_t> order;   // ticket -> tile linear index (problem bits added by callers)
 };
 
-// Tile (or column) extents the planner uses for these lengths and kernel.
-void tile_extents(int k, const int32_t *lens, int kernel, int32_t *E);
+// Tile (or column) extents the planner uses for these lengths, kernel and edge.
+void tile_extents(int k, const int32_t *lens, int kernel, int edge, int32_t *E);
+
+// Tuned choices per k (process-wide, thread-safe): the generic kernel's tile
+// edge (0 restores the default) and, for k = 3, whether the automatic choice
+// prefers the generic kernel over the column kernel.
+int tile_edge_for(int k);
+int set_tile_edge(int k, int edge);
+bool prefer_tiles_k3();
+void set_prefer_tiles_k3(bool v);
 
 // Fill `hp` for one problem. Returns MSA_OK or an MSA_E* code with `err` set.
-int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err);
+// edge < 0 takes the current tuned edge for k.
+int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err,
+              int edge = -1);
 
 // Units on each wave of a grid (tiles whose coordinates sum to w), w = 0, 1, ...
 void wave_sizes(int k, const int32_t *grid, std::vector<int64_t> &out);

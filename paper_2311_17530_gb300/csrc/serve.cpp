@@ -60,7 +60,7 @@ struct ServeReq {
 };
 
 struct Group {
-    int kernel = 0, k = 0, maxA = 1;
+    int kernel = 0, k = 0, edge = 0, maxA = 1;
     int first = 0, count = 0;  // slice of the batch's (sorted) requests
     int64_t tickets = 0, tiles = 0;
     size_t order_off = 0, done_off = 0;
@@ -396,18 +396,20 @@ void Server::run() {
 // Pack, enqueue (or capture and replay) one batch on the slot's stream.
 int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg) {
     // requests grouped by fill kernel and k; each group is one persistent launch
-    std::stable_sort(batch.begin(), batch.end(), [](const ServeReq *a, const ServeReq *b) {
-        return a->hp.kernel * 16 + a->k < b->hp.kernel * 16 + b->k;
-    });
+    auto gkey = [](const ServeReq *r) { return (r->hp.kernel * 16 + r->k) * 256 + r->hp.edge; };
+    std::stable_sort(batch.begin(), batch.end(),
+                     [&](const ServeReq *a, const ServeReq *b) { return gkey(a) < gkey(b); });
     sl.reqs = batch;
     const int n = (int)batch.size();
     std::vector<Group> groups;
     for (int i = 0; i < n; ++i) {
         const HostPlan &hp = batch[i]->hp;
-        if (groups.empty() || groups.back().kernel != hp.kernel || groups.back().k != hp.k) {
+        if (groups.empty() || groups.back().kernel != hp.kernel || groups.back().k != hp.k ||
+            groups.back().edge != hp.edge) {
             Group g;
             g.kernel = hp.kernel;
             g.k = hp.k;
+            g.edge = hp.edge;
             g.first = i;
             groups.push_back(g);
         }
@@ -540,7 +542,7 @@ int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg
             const HostPlan &hp = batch[g.first + keys[t].p]->hp;
             ord[t] = ((uint64_t)keys[t].p << 32) | hp.order[keys[t].tile];
         }
-        g.grid = persistent_grid(g.k, g.kernel, g.tickets, g.maxA);  // occupancy queries stay out of captures
+        g.grid = persistent_grid(g.k, g.kernel, g.tickets, g.maxA, g.edge);  // no occupancy query in a capture
     }
     bool col3 = false;
     for (const Group &g : groups) col3 = col3 || g.kernel == kKernelCol3;
@@ -559,7 +561,7 @@ int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg
     }
     const bool graphs = cfg.use_graphs && cfg.batching;
     uint64_t sig = 1469598103934665603ull;
-    for (const Group &g : groups) sig = (sig ^ (uint64_t)(g.kernel * 16 + g.k)) * 1099511628211ull;
+    for (const Group &g : groups) sig = (sig ^ (uint64_t)((g.kernel * 16 + g.k) * 256 + g.edge)) * 1099511628211ull;
     cudaError_t e = cudaSuccess;
     if (graphs) e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     int rc = MSA_OK;
@@ -582,7 +584,7 @@ int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg
         L.tab_ints = g.maxA * (g.maxA + 1) * 32;
         L.epoch = epoch_;
         e = g.kernel == kKernelCol3 ? launch_fill_col3(L, g.grid, col3_smem_bytes(g.maxA), s)
-                                    : launch_fill_tiles(g.k, L, g.grid, s);
+                                    : launch_fill_tiles(g.k, g.edge, L, g.grid, s);
     }
     if (e == cudaSuccess) e = launch_traceback(ddesc, n, &dstate[0].err, dio, IODesc{}, s);
     if (e == cudaSuccess)

@@ -31,7 +31,8 @@ _NAMES = {MSA_EINVAL: "MSA_EINVAL", MSA_ETOOBIG: "MSA_ETOOBIG", MSA_ENOMEM: "MSA
 EXPORTED = ["msa_align", "msa_last_error", "msa_set_stream", "msa_config", "msa_plan_create",
             "msa_plan_execute", "msa_plan_get_info", "msa_plan_destroy", "msa_submit", "msa_poll",
             "msa_cancel", "msa_drain", "msa_wave_sizes", "msa_tile_shape", "msa_version",
-            "msa_plan_read_tb", "msa_plan_timings", "msa_align_noalloc", "msa_wait_any"]
+            "msa_plan_read_tb", "msa_plan_timings", "msa_align_noalloc", "msa_wait_any",
+            "msa_set_tile_edge", "msa_get_tile_edge", "msa_autotune"]
 
 
 class MsaError(RuntimeError):
@@ -46,6 +47,16 @@ class PlanInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_int64), ("tile_grid", ctypes.c_int32 * MAX_K),
                 ("tile_extent", ctypes.c_int32 * MAX_K), ("tiles", ctypes.c_int64),
                 ("waves", ctypes.c_int32), ("fill_kernel", ctypes.c_int32), ("d_tb", ctypes.c_void_p)]
+
+
+MAX_TUNING_CANDIDATES = 8
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("ncand", ctypes.c_int32),
+                ("cand_kernel", ctypes.c_int32 * MAX_TUNING_CANDIDATES),
+                ("cand_edge", ctypes.c_int32 * MAX_TUNING_CANDIDATES),
+                ("cand_ms", ctypes.c_float * MAX_TUNING_CANDIDATES), ("best", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):
@@ -87,6 +98,9 @@ def library() -> ctypes.CDLL:
     L.msa_poll.argtypes = [ctypes.c_uint64, i32p, ctypes.c_char_p]
     L.msa_cancel.argtypes = [ctypes.c_uint64]
     L.msa_wait_any.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
+    L.msa_set_tile_edge.argtypes = [ctypes.c_int, ctypes.c_int32]
+    L.msa_get_tile_edge.argtypes = [ctypes.c_int, i32p]
+    L.msa_autotune.argtypes = [ctypes.c_int, i32p, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(Tuning)]
     L.msa_wave_sizes.argtypes = [ctypes.c_int, i32p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, i32p]
     L.msa_tile_shape.argtypes = [ctypes.c_int, i32p, i32p, i32p]
     _lib = L
@@ -265,6 +279,26 @@ def msa_cancel(handle: int) -> None:
 
 def msa_drain() -> None:
     _check(library().msa_drain())
+
+
+def msa_set_tile_edge(k: int, edge: int) -> None:
+    _check(library().msa_set_tile_edge(int(k), int(edge)))
+
+
+def msa_get_tile_edge(k: int) -> int:
+    e = ctypes.c_int32(0)
+    _check(library().msa_get_tile_edge(int(k), ctypes.byref(e)))
+    return int(e.value)
+
+
+def msa_autotune(lens: Sequence[int], alphabet_size: int, repeats: int = 3) -> dict:
+    """Time the compiled tile shapes (and the k=3 column kernel) for this shape; the
+    fastest becomes the choice for k. Returns the candidates and the choice."""
+    t = Tuning()
+    _check(library().msa_autotune(len(lens), _i32(lens), int(alphabet_size), int(repeats), ctypes.byref(t)))
+    cands = [{"kernel": "column" if t.cand_kernel[i] == 2 else "tiles", "edge": int(t.cand_edge[i]),
+              "ms": float(t.cand_ms[i])} for i in range(t.ncand)]
+    return {"k": int(t.k), "lens": list(lens), "candidates": cands, "best": cands[t.best]}
 
 
 def msa_wait_any(timeout_us: int) -> Optional[int]:
