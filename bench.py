@@ -280,6 +280,21 @@ def run_serving(n: int):
             "speedup_closed_loop": batched["alignments_per_s"] / plain["alignments_per_s"], "poisson_sweep": sweep}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Units all ranks processed (weak scaling: every rank its own replica) over the max time."""
+    return units_per_rank * world / seconds_max
+
+
 def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -375,13 +390,11 @@ def run_gb300(args, rank, world, local):
     msadp.msa_config("timing", 0)
     ms_total = ev0.elapsed_time(ev1)
     enc_ms, fill_ms, tb_ms = plan.timings()
+    ms_total = max_over_ranks(ms_total, dist, dev)
     if dist:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
         dist.barrier()
     ms_step = ms_total / args.steps
-    value = p.cells * world / (ms_step / 1e3)
+    value = whole_job_rate(p.cells, world, ms_step / 1e3)
 
     # end to end through the public C-ABI with host buffers
     e2e = None
@@ -394,13 +407,8 @@ def run_gb300(args, rank, world, local):
             s2, _ = msadp.msa_align(p.seqs, p.alphabet, p.subst, p.gap)
             ts.append(time.perf_counter() - t0)
             assert s2 == score
-        if dist:
-            t = torch.tensor([sum(ts)], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        else:
-            tot = sum(ts)
-        e2e = {"value": p.cells * world * args.steps / tot, "unit": UNIT,
+        tot = max_over_ranks(sum(ts), dist, dev)
+        e2e = {"value": whole_job_rate(p.cells * args.steps, world, tot), "unit": UNIT,
                "h2d_bytes_per_step": total_len + p.subst.size * 4,
                "d2h_bytes_per_step": 16 + total_len, "ms_per_step": 1e3 * tot / args.steps}
 

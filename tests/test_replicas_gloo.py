@@ -1,0 +1,51 @@
+"""The N > 1 path of bench.py on the CPU: two gloo ranks (127.0.0.1), each with
+its own replica time; every rank must see the slowest rank's time, and the
+whole-job rate counts the units of all ranks over that time."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        mine = 10.0 + 5.0 * rank  # ms of this replica
+        slowest = bench.max_over_ranks(mine, dist, torch.device("cpu"))
+        rate = bench.whole_job_rate(1000.0, world, slowest / 1e3)
+        dist.barrier()
+        q.put((rank, slowest, rate))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_max_time_and_sum_units():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(world))
+    for rank, slowest, rate in got:
+        assert slowest == 15.0                     # max over ranks, on every rank
+        assert rate == pytest.approx(2 * 1000.0 / 0.015)
