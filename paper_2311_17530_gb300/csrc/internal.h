@@ -160,13 +160,11 @@ __host__ __device__ constexpr int face1_rows(int rho2) { return nsteps(rho2) + U
 __host__ __device__ constexpr int64_t tb_col_bytes(int rho2) { return (int64_t)(nsteps(rho2) + U) * W * 32 * R; }
 }  // namespace c3
 
-// Traceback box edge D per k (the box [x-D, x] is staged in shared memory; rows
-// along the last axis are copied in granules of traceback_granule(k) bytes, so a
-// staged row holds at most round_up(D + granule, granule) bytes).
-__host__ __device__ constexpr int traceback_box(int k) {
-    return k == 2 ? 192 : k == 3 ? 28 : k == 4 ? 11 : k == 5 ? 7 : k == 6 ? 4 : k == 7 ? 3 : 2;
-}
-__host__ __device__ constexpr int traceback_granule(int k) { return k <= 4 ? 16 : 4; }
+// Traceback box edge D for the row-major layout with k <= 3 (the box [x-D, x] is
+// staged in shared memory, rows along the last axis in 16-byte granules, so a
+// staged row holds at most round_up(D + 16, 16) bytes); larger k reads cells
+// directly.
+__host__ __device__ constexpr int traceback_box(int k) { return k == 2 ? 192 : 28; }
 constexpr int kTracebackSmem = 72 * 1024;
 // The traceback tensor's last axis is padded to this many bytes (16-byte rows).
 constexpr int kTbRowAlign = 16;
@@ -203,6 +201,7 @@ cudaError_t launch_encode(const ProblemDesc *d_probs, int nprob, int max_ncode,
                           const IODesc *io_array, IODesc io_single, cudaStream_t s);
 cudaError_t launch_fill_tiles(int k, int edge, const LaunchDesc &L, int grid, cudaStream_t s);
 cudaError_t prepare_kernel_attributes();
+cudaError_t traceback_attributes();
 int fill_tiles_ctas_per_sm(int k, int edge);
 int fill_tiles_warps_per_cta(int k, int edge);
 cudaError_t launch_fill_col3(const LaunchDesc &L, int grid, int smem, cudaStream_t s);

@@ -1,0 +1,325 @@
+// Traceback (section 2): from the far corner follow the stored move of every
+// cell back to the origin, then score the path.
+//
+// One CTA of 256 threads per problem. The walk is a chain of dependent reads, so
+// thread 0 walks; the rest of the CTA stages the data it reads:
+//   * column layout (k = 3 column kernel): windows of kTbcT CTA times x every
+//     warp block x every lane of one column (64 KB, cp.async by all threads);
+//     every move lowers the CTA time T = x2 + l + (x0 mod WR) by its popcount,
+//     so a window holds at least kTbcT / 3 moves unless the walk leaves the column;
+//   * row-major layout, k <= 3: boxes [x - D, x] (rows of the last axis copied in
+//     16-byte granules);
+//   * row-major layout, k >= 4 (short paths, large boxes): no staging; warp 0
+//     loads the traceback bytes of the current cell and of all its predecessors
+//     in one round trip, which fixes two moves.
+// The walk records only the masks (last column first). The score is computed
+// afterwards by the whole CTA: each thread takes a contiguous run of columns,
+// the per-axis move counts are prefix-summed to give each column's position, and
+// the column scores u*|m| + sum over moved pairs of (sub - 2 gap) are added up.
+// For the generic tile kernel the sum is cross-checked against the corner's
+// packed key.
+#include "api_internal.h"
+#include "device_common.cuh"
+
+namespace msadp {
+namespace {
+
+constexpr int kTbThreads = 256;
+constexpr int kTbcT = 64;                                   // CTA times per column window
+constexpr int kTbcBytes = kTbcT * c3::W * 32 * c3::R;       // 64 KB
+static_assert(kTbcBytes <= kTracebackSmem, "traceback window exceeds its shared memory");
+
+__device__ __forceinline__ void cp_async_16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+struct WalkState {
+    int x[MSA_MAX_K];
+    int ncols;
+    int fail;
+};
+
+// Validates a move at position x and records it; false ends the walk with a failure.
+__device__ __forceinline__ bool take_move(int K, int m, int *x, const ProblemDesc &P, const IODesc &io, int &ncols) {
+    bool bad = m == 0 || (m >> K) != 0 || ncols >= P.len_sum;
+    for (int i = 0; i < K; ++i)
+        if (((m >> i) & 1) && x[i] == 0) bad = true;
+    if (bad) return false;
+    io.masks[ncols++] = (uint8_t)m;
+    for (int i = 0; i < K; ++i) x[i] -= (m >> i) & 1;
+    return true;
+}
+
+__device__ __forceinline__ bool at_origin(int K, const int *x) {
+    for (int i = 0; i < K; ++i)
+        if (x[i] != 0) return false;
+    return true;
+}
+
+// Column layout of the k = 3 column kernel.
+__device__ void walk_col3(const ProblemDesc &P, const IODesc &io, unsigned char *win, WalkState &ws) {
+    const int tid = threadIdx.x;
+    const int NB = P.G[1];
+    const int rho2 = P.rho[2];
+    const int64_t colb = c3::tb_col_bytes(rho2);
+    const int nT = c3::nsteps(rho2);
+    while (true) {
+        __syncthreads();
+        if (ws.fail || at_origin(3, ws.x)) break;
+        const int x0 = ws.x[0], x1 = ws.x[1], x2 = ws.x[2];
+        const int cA = x0 / c3::WR, cB = x1 >> 5;
+        const int t_lo = x2 + (x1 & 31) + x0 % c3::WR - (kTbcT - 1);
+        const unsigned char *col = P.tb + (int64_t)(cA * NB + cB) * colb;
+        // window rows: CTA times [t_lo, t_lo + kTbcT), all warp blocks and lanes (1024 B per time)
+        for (int i = tid; i < kTbcBytes / 16; i += kTbThreads) {
+            const int tt = t_lo + i / (c3::W * 32 * c3::R / 16);
+            if (tt >= 0 && tt < nT)
+                cp_async_16(win + 16 * i, col + (int64_t)(tt + c3::U) * (c3::W * 32 * c3::R) +
+                                              16 * (i % (c3::W * 32 * c3::R / 16)));
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (tid == 0) {
+            int *x = ws.x;
+            const int before = ws.ncols;
+            while (!at_origin(3, x)) {
+                const int rho = x[0] % c3::WR, l = x[1] & 31;
+                const int tt = x[2] + l + rho;
+                if (x[0] / c3::WR != cA || (x[1] >> 5) != cB || tt < t_lo) break;
+                const int m = win[((tt - t_lo) * c3::W + rho / c3::R) * (32 * c3::R) + l * c3::R + rho % c3::R];
+                if (!take_move(3, m, x, P, io, ws.ncols)) {
+                    ws.fail = 1;
+                    break;
+                }
+            }
+            if (ws.ncols == before && !at_origin(3, x)) ws.fail = 1;  // a window must advance the walk
+        }
+    }
+}
+
+// Row-major layout, boxes [x - D, x] (k <= 3).
+__device__ void walk_boxes(const ProblemDesc &P, const IODesc &io, unsigned char *box, WalkState &ws) {
+    const int tid = threadIdx.x;
+    const int K = P.k;
+    const int D = traceback_box(K);
+    constexpr int G = 16;
+    int64_t ts[MSA_MAX_K];
+    for (int i = 0; i < K; ++i) ts[i] = P.tbstride[i];
+    while (true) {
+        __syncthreads();
+        if (ws.fail || at_origin(K, ws.x)) break;
+        int lo[MSA_MAX_K], ext[MSA_MAX_K];
+        int64_t bs[MSA_MAX_K];
+        for (int i = 0; i < K; ++i) lo[i] = max(0, ws.x[i] - D);
+        const int a = lo[K - 1] & ~(G - 1);
+        const int rowb = round_up(ws.x[K - 1] - a + 1, G);
+        const int cpr = rowb / G;
+        bs[K - 1] = 1;
+        int64_t stride = rowb;
+        int rows = 1;
+        for (int i = K - 2; i >= 0; --i) {
+            bs[i] = stride;
+            ext[i] = ws.x[i] - lo[i] + 1;
+            stride *= ext[i];
+            rows *= ext[i];
+        }
+        for (int idx = tid; idx < rows * cpr; idx += kTbThreads) {
+            int r = idx / cpr;
+            const int c = idx - r * cpr;
+            const int row = r;
+            int64_t g = a;
+            for (int i = K - 2; i >= 0; --i) {
+                const int ci = r % ext[i];
+                r /= ext[i];
+                g += (int64_t)(lo[i] + ci) * ts[i];
+            }
+            cp_async_16(box + (int64_t)row * rowb + 16 * c, P.tb + g + 16 * c);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (tid == 0) {
+            int *x = ws.x;
+            const int before = ws.ncols;
+            int64_t li = x[K - 1] - a;
+            for (int i = 0; i < K - 1; ++i) li += (int64_t)(x[i] - lo[i]) * bs[i];
+            while (!at_origin(K, x)) {
+                const int m = box[li];
+                if (!take_move(K, m, x, P, io, ws.ncols)) {
+                    ws.fail = 1;
+                    break;
+                }
+                bool out = false;
+                for (int i = 0; i < K; ++i)
+                    if ((m >> i) & 1) {
+                        li -= bs[i];
+                        if (x[i] < lo[i]) out = true;
+                    }
+                if (out) break;
+            }
+            if (ws.ncols == before && !at_origin(K, x)) ws.fail = 1;  // a box must advance the walk
+        }
+    }
+}
+
+// Row-major layout, k >= 4: the current cell and all its predecessors per round trip.
+__device__ void walk_direct(const ProblemDesc &P, const IODesc &io, unsigned char *pred, WalkState &ws) {
+    const int tid = threadIdx.x;
+    const int K = P.k;
+    const int NM = (1 << K) - 1;
+    if (tid >= 32) return;
+    int x[MSA_MAX_K];
+    for (int i = 0; i < K; ++i) x[i] = ws.x[i];
+    int ncols = 0, fail = 0;
+    while (!fail && !at_origin(K, x)) {
+        // slot 0: the cell itself; slot m: its predecessor x - e_m (if inside)
+        for (int m = tid; m <= NM; m += 32) {
+            int64_t g = 0;
+            bool in = true;
+            for (int i = 0; i < K; ++i) {
+                const int c = x[i] - ((m >> i) & 1);
+                in = in && c >= 0;
+                g += (int64_t)c * P.tbstride[i];
+            }
+            pred[m] = in ? __ldcg(P.tb + g) : (unsigned char)0;
+        }
+        __syncwarp();
+        if (tid == 0) {
+            const int m1 = pred[0];
+            if (!take_move(K, m1, x, P, io, ncols)) {
+                fail = 1;
+            } else if (!at_origin(K, x) && !take_move(K, pred[m1], x, P, io, ncols)) {
+                fail = 1;
+            }
+        }
+        __syncwarp();
+        for (int i = 0; i < K; ++i) x[i] = __shfl_sync(kFull, x[i], 0);
+        fail = __shfl_sync(kFull, fail, 0);
+        ncols = __shfl_sync(kFull, ncols, 0);
+    }
+    if (tid == 0) {
+        for (int i = 0; i < K; ++i) ws.x[i] = x[i];
+        ws.ncols = ncols;
+        ws.fail = fail;
+    }
+}
+
+// Score of the recorded path, by the whole CTA: sum over columns of
+// u*|m| + sum over moved pairs (sub - 2 gap), each column at the position the
+// suffix of later moves (earlier in the record) gives it.
+__device__ int score_path(const ProblemDesc &P, const IODesc &io, int ncols, int *scan) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = P.k, B = P.B, A = P.A;
+    const int u = io.gap * (K - 1);
+    const int per = (ncols + kTbThreads - 1) / kTbThreads;
+    const int j0 = min(ncols, tid * per), j1 = min(ncols, j0 + per);
+    // moves per axis in this thread's run, then an exclusive scan over threads
+    int cnt[MSA_MAX_K] = {};
+    for (int j = j0; j < j1; ++j) {
+        const int m = io.masks[j];
+        for (int i = 0; i < K; ++i) cnt[i] += (m >> i) & 1;
+    }
+    int off[MSA_MAX_K];
+    for (int i = 0; i < K; ++i) {
+        int v = cnt[i];
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(kFull, v, d);
+            if (lane >= d) v += y;
+        }
+        if (lane == 31) scan[i * 8 + warp] = v;
+        off[i] = v - cnt[i];
+    }
+    __syncthreads();
+    for (int i = 0; i < K; ++i)
+        for (int w2 = 0; w2 < warp; ++w2) off[i] += scan[i * 8 + w2];
+    int x[MSA_MAX_K];
+    for (int i = 0; i < K; ++i) x[i] = P.len[i] - off[i];
+    int s = 0;
+    for (int j = j0; j < j1; ++j) {
+        const int m = io.masks[j];
+        int c[MSA_MAX_K], nm = 0;
+        for (int i = 0; i < K; ++i)
+            if ((m >> i) & 1) c[nm++] = P.codes[P.cofs[i] + x[i] - 1];
+        int col = u * nm;
+        for (int a = 0; a < nm; ++a)
+            for (int b = a + 1; b < nm; ++b) col += P.tab[c[a] * A + c[b]] >> B;
+        s += col;
+        for (int i = 0; i < K; ++i) x[i] -= (m >> i) & 1;
+    }
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(kFull, s, d);
+    __syncthreads();
+    if (lane == 0) scan[64 + warp] = s;
+    __syncthreads();
+    int total = 0;
+    for (int w2 = 0; w2 < kTbThreads / 32; ++w2) total += scan[64 + w2];
+    return total;
+}
+
+__global__ void __launch_bounds__(kTbThreads) traceback_kernel(const ProblemDesc *probs, const int32_t *err,
+                                                               const IODesc *io_arr, IODesc io1) {
+    const int p = blockIdx.x;
+    const ProblemDesc &P = probs[p];
+    const IODesc io = io_arr ? io_arr[p] : io1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ WalkState ws;
+    __shared__ int scan[64 + kTbThreads / 32];
+    const int tid = threadIdx.x;
+    int status = ld_volatile(&P.istat->status);
+    if (status == 0 && err) status = ld_volatile(err);
+    if (status != 0) {
+        if (tid == 0) {
+            io.result->status = status;
+            io.result->score = 0;
+            io.result->ncols = 0;
+        }
+        return;
+    }
+    const int K = P.k;
+    if (tid == 0) {
+        for (int i = 0; i < K; ++i) ws.x[i] = P.len[i];
+        ws.ncols = 0;
+        ws.fail = 0;
+    }
+    __syncthreads();
+    if (P.tb_layout == 1)
+        walk_col3(P, io, smem, ws);
+    else if (K <= 3)
+        walk_boxes(P, io, smem, ws);
+    else
+        walk_direct(P, io, smem, ws);
+    __syncthreads();
+    const int ncols = ws.ncols;
+    int fail = ws.fail;
+    const int score = fail ? 0 : score_path(P, io, ncols, scan);
+    if (tid == 0) {
+        if (!fail && P.has_qcorner) {
+            // cross-check against the fill's own corner value: q = H' * 2^B + W(corner)
+            const int q = *P.qcorner;
+            const int h = ((q - P.w_corner) >> P.B) + io.gap * (K - 1) * P.len_sum;
+            if (h != score) fail = 1;
+        }
+        io.result->score = score;
+        io.result->ncols = ncols;
+        io.result->status = fail ? MSA_ECUDA : MSA_OK;
+    }
+}
+
+}  // namespace
+
+cudaError_t traceback_attributes() {
+    static DeviceOnce once;  // attribute set once per device, never inside a stream capture
+    return once.run([] {
+        return cudaFuncSetAttribute(traceback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTracebackSmem);
+    });
+}
+
+cudaError_t launch_traceback(const ProblemDesc *d_probs, int nprob, const int32_t *err,
+                             const IODesc *io_array, IODesc io_single, cudaStream_t s) {
+    cudaError_t e = traceback_attributes();
+    if (e != cudaSuccess) return e;
+    traceback_kernel<<<nprob, kTbThreads, kTracebackSmem, s>>>(d_probs, err, io_array, io_single);
+    return cudaGetLastError();
+}
+
+}  // namespace msadp
