@@ -42,7 +42,7 @@
 // Cell update with pair scores scaled by 2^3 (packed keys, see internal.h): the
 // max over the seven moves gives the key, then m* = (W(x) - max) mod 8 and
 // Q(x) = max + m*; m* is the traceback byte. Each lane stores its R bytes of a
-// step as one 4-byte word, 128 contiguous bytes per warp step.
+// step as one word, 32 * R contiguous bytes per warp step.
 #include "api_internal.h"
 #include "device_common.cuh"
 
@@ -152,7 +152,7 @@ struct C3Blk {
     const unsigned long long *rin;  // ring[w][T0 mod SI][lane]
     unsigned long long *rout;       // ring[w+1][T0 mod SI][lane] or F0[T0][lane] (generic)
     const int *f1row;               // f1r[T0 mod SF]
-    unsigned *tbp;                  // traceback word of (T0, w, lane)
+    unsigned char *tbp;             // traceback bytes of (T0, w, lane): R bytes
     unsigned long long *f1o;        // F1[T0][wR]
     const uint16_t *c2p;            // code offset of x2 = T0 + 2 - lane - wR
 };
@@ -162,12 +162,19 @@ __device__ __forceinline__ void c3_step(C3St &g, const C3Ln &c, const char *tab,
                                         C3Smem &sm, const LaunchDesc &L) {
     constexpr int M = 2 * c3::R - 1;
     constexpr int R = c3::R;
+    static_assert(R == 2 || R == 4, "rows per warp: 2 or 4");
     const int T = T0 + s;
     // U(T, r) from lane l-1 (lane 0: the staged face)
     const int *fr = b.f1row + s * c3::F1S;
-    const int4 f = *reinterpret_cast<const int4 *>(fr + 4 + c.wR);
+    int fv[R];
+    if constexpr (R == 4) {
+        const int4 f = *reinterpret_cast<const int4 *>(fr + 4 + c.wR);
+        fv[0] = f.x, fv[1] = f.y, fv[2] = f.z, fv[3] = f.w;
+    } else {
+        const int2 f = *reinterpret_cast<const int2 *>(fr + 4 + c.wR);
+        fv[0] = f.x, fv[1] = f.y;
+    }
     const int fm = fr[3 + c.wR];
-    const int fv[4] = {f.x, f.y, f.z, f.w};
     int Un[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -188,11 +195,15 @@ __device__ __forceinline__ void c3_step(C3St &g, const C3Ln &c, const char *tab,
     }
     // outputs: last row to the warp below (or face F0), traceback bytes, lane 31 to face F1
     st_entry(b.rout + s * 32, pack_entry(g.V[R - 1], c.tagout + T));
-    b.tbp[s * (c3::W * 32)] = pk;
+    if constexpr (R == 4)
+        *reinterpret_cast<uint32_t *>(b.tbp + s * (c3::W * 32 * R)) = pk;
+    else
+        *reinterpret_cast<uint16_t *>(b.tbp + s * (c3::W * 32 * R)) = (uint16_t)pk;
     if (c.last) {
         const int tg = c.tagf1 + T;
-        st_global_v2(b.f1o + s * c3::WR, pack_entry(g.V[0], tg), pack_entry(g.V[1], tg));
-        st_global_v2(b.f1o + s * c3::WR + 2, pack_entry(g.V[2], tg), pack_entry(g.V[3], tg));
+#pragma unroll
+        for (int r = 0; r < R; r += 2)
+            st_global_v2(b.f1o + s * c3::WR + r, pack_entry(g.V[r], tg), pack_entry(g.V[r + 1], tg));
     }
     // code of the position x2 = T + 2 - lane - wR (row 0 of time T + 2)
     const int cn = b.c2p[s];
@@ -230,13 +241,19 @@ struct C3Col {
 // the number of CTA-time rows staged. Positions a producer never computes (past
 // its last step, or no producer at all) are staged as kNeg. A batch covers SB
 // rows: every load of the batch is issued before any tag is checked (one L2 round
-// trip per batch); a face row is 32 entries of 8 bytes, read by half a warp as
-// 16-byte pairs, so one load instruction covers two rows.
+// trip per batch). Loads are 16-byte pairs of entries: an F0 row (32 entries) is
+// read by half a warp, an F1 row (WR entries) by WR / 2 lanes.
 __device__ void c3_stager(C3Smem &sm, const C3Col &cc, int lane, const LaunchDesc &L) {
-    constexpr int SB = 16;                 // rows per batch
-    constexpr int NL = SB / 2;             // vector loads per face and lane
+    constexpr int SB = 16;                       // rows per batch
+    constexpr int NL0 = SB / 2;                  // F0 loads per lane and batch (2 rows per load)
+    constexpr int LPR1 = c3::WR / 2;             // lanes per F1 row
+    constexpr int RPI1 = 32 / LPR1;              // F1 rows per load
+    constexpr int NL1 = SB / RPI1;               // F1 loads per lane and batch
     static_assert(SB <= c3::SI - c3::U && SB <= c3::SF - c3::U, "staging batch exceeds the rings");
-    const int half = lane >> 4, pair = 2 * (lane & 15);  // row parity and first entry of this lane
+    static_assert(SB % RPI1 == 0 && 32 % LPR1 == 0, "F1 rows per load");
+    const int half = lane >> 4, pair0 = 2 * (lane & 15);            // F0: row parity, first entry
+    const int sub1 = lane / LPR1, pair1 = 2 * (lane % LPR1);        // F1: row in the load, first entry
+    const unsigned rowmask1 = LPR1 == 32 ? 0xffffffffu : ((1u << LPR1) - 1);
     int Ts = -c3::U;
     uint64_t t_progress = global_ns();
     while (Ts < cc.N) {
@@ -259,18 +276,22 @@ __device__ void c3_stager(C3Smem &sm, const C3Col &cc, int lane, const LaunchDes
             }
         }
         // issue every load of the batch
-        ulonglong2 a[NL], b[NL];
+        ulonglong2 a[NL0], b[NL1];
         unsigned long long d = pack_entry(kNeg, 0);
         const ulonglong2 none = make_ulonglong2(pack_entry(kNeg, 0), pack_entry(kNeg, 0));
 #pragma unroll
-        for (int i = 0; i < NL; ++i) {
+        for (int i = 0; i < NL0; ++i) {
             const int T = Ts + 2 * i + half;
             a[i] = none;
-            b[i] = none;
             if (cc.f0up && T + c3::WR < cc.N)
-                a[i] = ld_global_relaxed_v2(cc.f0up + (int64_t)(T + c3::WR + c3::U) * 32 + pair);
+                a[i] = ld_global_relaxed_v2(cc.f0up + (int64_t)(T + c3::WR + c3::U) * 32 + pair0);
+        }
+#pragma unroll
+        for (int i = 0; i < NL1; ++i) {
+            const int T = Ts + RPI1 * i + sub1;
+            b[i] = none;
             if (cc.f1left && T + 31 < cc.N)
-                b[i] = ld_global_relaxed_v2(cc.f1left + (int64_t)(T + 31 + c3::U) * c3::WR + pair);
+                b[i] = ld_global_relaxed_v2(cc.f1left + (int64_t)(T + 31 + c3::U) * c3::WR + pair1);
         }
         {
             const int T = Ts + lane;  // lane i fetches the corner of row Ts + i
@@ -280,21 +301,32 @@ __device__ void c3_stager(C3Smem &sm, const C3Col &cc, int lane, const LaunchDes
         // rows whose entries all carry this launch's tag
         unsigned rows_ok = 0;
 #pragma unroll
-        for (int i = 0; i < NL; ++i) {
+        for (int i = 0; i < NL0; ++i) {
             const int T = Ts + 2 * i + half;
             bool v = true;
             if (cc.f0up && T + c3::WR < cc.N) {
                 const int want = cc.tagbase + T + c3::WR;
-                v = v && (int)(a[i].x >> 32) == want && (int)(a[i].y >> 32) == want;
-            }
-            if (cc.f1left && T + 31 < cc.N) {
-                const int want = cc.tagbase + T + 31;
-                v = v && (int)(b[i].x >> 32) == want && (int)(b[i].y >> 32) == want;
+                v = (int)(a[i].x >> 32) == want && (int)(a[i].y >> 32) == want;
             }
             const unsigned bal = __ballot_sync(kFull, v);
             rows_ok |= ((bal & 0xffffu) == 0xffffu ? 1u : 0u) << (2 * i);
             rows_ok |= ((bal >> 16) == 0xffffu ? 1u : 0u) << (2 * i + 1);
         }
+        unsigned rows_ok1 = 0;
+#pragma unroll
+        for (int i = 0; i < NL1; ++i) {
+            const int T = Ts + RPI1 * i + sub1;
+            bool v = true;
+            if (cc.f1left && T + 31 < cc.N) {
+                const int want = cc.tagbase + T + 31;
+                v = (int)(b[i].x >> 32) == want && (int)(b[i].y >> 32) == want;
+            }
+            const unsigned bal = __ballot_sync(kFull, v);
+#pragma unroll
+            for (int q = 0; q < RPI1; ++q)
+                rows_ok1 |= (((bal >> (q * LPR1)) & rowmask1) == rowmask1 ? 1u : 0u) << (RPI1 * i + q);
+        }
+        rows_ok &= rows_ok1;
         {
             const int T = Ts + lane;
             const bool v = lane >= SB || !cc.f1diag || T + 31 + c3::WR >= cc.N ||
@@ -303,13 +335,20 @@ __device__ void c3_stager(C3Smem &sm, const C3Col &cc, int lane, const LaunchDes
         }
         const int n = rows_ok == (1u << SB) - 1 ? SB : __ffs(~rows_ok) - 1;  // rows ready, in order
 #pragma unroll
-        for (int i = 0; i < NL; ++i) {
+        for (int i = 0; i < NL0; ++i) {
             const int r = 2 * i + half;
             if (r < n) {
                 const int T = Ts + r;
-                *reinterpret_cast<ulonglong2 *>(&sm.ring[0][T & (c3::SI - 1)][pair]) =
+                *reinterpret_cast<ulonglong2 *>(&sm.ring[0][T & (c3::SI - 1)][pair0]) =
                     make_ulonglong2(pack_entry((int)(unsigned)a[i].x, T), pack_entry((int)(unsigned)a[i].y, T));
-                *reinterpret_cast<int2 *>(&sm.f1r[T & (c3::SF - 1)][4 + pair]) =
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NL1; ++i) {
+            const int r = RPI1 * i + sub1;
+            if (r < n) {
+                const int T = Ts + r;
+                *reinterpret_cast<int2 *>(&sm.f1r[T & (c3::SF - 1)][4 + pair1]) =
                     make_int2((int)(unsigned)b[i].x, (int)(unsigned)b[i].y);
             }
         }
@@ -468,8 +507,7 @@ __global__ void __launch_bounds__(c3::THREADS, 1) fill_col3_kernel(const LaunchD
             g.cc[0] = g.pp[0] = 0;
 
             unsigned long long *ringout = lastw ? cc.f0dst + lane : &sm.ring[w + 1][0][lane];
-            unsigned *tbw = reinterpret_cast<unsigned *>(P.tb + (int64_t)lin * c3::tb_col_bytes(P.rho[2])) +
-                            w * 32 + lane;
+            unsigned char *tbw = P.tb + (int64_t)lin * c3::tb_col_bytes(P.rho[2]) + (w * 32 + lane) * c3::R;
             for (int T0 = -c3::U; T0 < cc.N; T0 += c3::U) {
                 if (!c3_block_wait(sm, w, T0, L)) break;
                 if (T0 == 0 && origin) g.P[0] = 0;  // H(0) = 0, no move
@@ -477,7 +515,7 @@ __global__ void __launch_bounds__(c3::THREADS, 1) fill_col3_kernel(const LaunchD
                 b.rin = &sm.ring[w][T0 & (c3::SI - 1)][lane];
                 b.rout = lastw ? ringout + (int64_t)(T0 + c3::U) * 32 : ringout + (T0 & (c3::SI - 1)) * 32;
                 b.f1row = &sm.f1r[T0 & (c3::SF - 1)][0];
-                b.tbp = tbw + (int64_t)(T0 + c3::U) * (c3::W * 32);
+                b.tbp = tbw + (int64_t)(T0 + c3::U) * (c3::W * 32 * c3::R);
                 b.f1o = cc.f1dst + (int64_t)(T0 + c3::U) * c3::WR + c.wR;
                 b.c2p = c2lane + T0;
                 c3_step<0>(g, c, tab, b, T0, lane, sm, L);

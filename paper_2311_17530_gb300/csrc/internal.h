@@ -137,7 +137,7 @@ constexpr int MAXA = 24;      // largest alphabet (replicated pair table)
 constexpr int MAXRHO2 = 4096; // largest axis-2 extent (staged codes)
 constexpr int CODEPAD = 96;   // axis-2 code staging pad on both sides
 constexpr int kSentinelPair = -(1 << 27);  // pair score of a move into x2 <= 0 (no residue)
-static_assert(U % (2 * R) == 0 && SI % U == 0 && SF % U == 0 && WR == 32, "column geometry");
+static_assert(U % (2 * R) == 0 && SI % U == 0 && SF % U == 0 && (WR == 16 || WR == 32), "column geometry");
 // CTA-time steps of one column: the last cell x2 = rho2 - 1 of lane 31, row
 // WR - 1 is computed at T = rho2 + WR + 29; rounded up to whole blocks. A column
 // runs T = -U .. nsteps - 1: the first block only fills the pipeline (its cells
