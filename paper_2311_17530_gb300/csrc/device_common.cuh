@@ -113,6 +113,14 @@ __host__ __device__ constexpr int highbit_c(int m) {
     }
     return h;
 }
+__host__ __device__ constexpr int lowbit_c(int m) {  // index of the lowest set bit
+    int l = 0;
+    while (m && !(m & 1)) {
+        m >>= 1;
+        ++l;
+    }
+    return l;
+}
 __host__ __device__ constexpr int round_up(int x, int a) { return (x + a - 1) / a * a; }
 
 }  // namespace msadp

@@ -232,36 +232,32 @@ fill_tiles_kernel(const LaunchDesc L) {
                     int a[K];
 #pragma unroll
                     for (int j = 0; j < K; ++j) a[j] = tcs[geo_code_base(K, E, j) + c[j]];
-                    int pv[K][K];
+                    // Candidates grouped by the move's highest sequence h. The pair
+                    // sum of m = r | 2^h is S[r] + T[r] with T[r] = sum_{l in r}
+                    // (scaled pair l, h); S is stored only below 2^(K-1), the top
+                    // group is consumed as it is formed, so the live state stays
+                    // small enough for registers.
+                    int acc = kNeg;
 #pragma unroll
-                    for (int i = 0; i < K; ++i)
-#pragma unroll
-                        for (int j = i + 1; j < K; ++j) pv[i][j] = __ldg(tab + a[i] * A + a[j]);
-                    // S[m] = sum of scaled pair scores over pairs inside move m,
-                    // built by highest element: S[r | h] = S[r] + T_h[r],
-                    // T_h[r] = sum_{l in r} pv[l][h].
-                    int S[NM + 1];
+                    for (int i = 0; i < K; ++i) acc = max(acc, qs[soff - geo_sh(K, E, i)]);
+                    int S[1 << (K - 1)];
                     S[0] = 0;
+                    S[1] = 0;  // the singleton {0}: no pair
 #pragma unroll
-                    for (int h = 0; h < K; ++h) {
+                    for (int h = 1; h < K; ++h) {
+                        int ph[K];
+#pragma unroll
+                        for (int l = 0; l < h; ++l) ph[l] = __ldg(tab + a[l] * A + a[h]);
                         int T[1 << (K - 1)];
                         T[0] = 0;
 #pragma unroll
-                        for (int r2 = 1; r2 < (1 << h); ++r2) {
-                            const int l = highbit_c(r2);
-                            T[r2] = T[r2 ^ (1 << l)] + pv[l][h];
+                        for (int r2 = 1; r2 < (1 << h); ++r2) T[r2] = T[r2 & (r2 - 1)] + ph[lowbit_c(r2)];
+#pragma unroll
+                        for (int r2 = 0; r2 < (1 << h); ++r2) {
+                            const int sm = S[r2] + T[r2];
+                            if (h < K - 1) S[r2 | (1 << h)] = sm;
+                            if (r2 != 0) acc = __viaddmax_s32(qs[soff - move_soff(K, E, r2 | (1 << h))], sm, acc);
                         }
-#pragma unroll
-                        for (int r2 = 0; r2 < (1 << h); ++r2) S[r2 | (1 << h)] = S[r2] + T[r2];
-                    }
-                    int acc = kNeg;
-#pragma unroll
-                    for (int m = 1; m <= NM; ++m) {
-                        const int pred = qs[soff - move_soff(K, E, m)];
-                        if (popc_c(m) == 1)
-                            acc = max(acc, pred);
-                        else
-                            acc = __viaddmax_s32(pred, S[m], acc);
                     }
                     const int tmask = (Wo + wl - acc) & MASKB;
                     qs[soff] = acc + tmask;
