@@ -444,11 +444,33 @@ int msa_plan_read_tb(msa_plan *plan, void *host_dst, int64_t bytes) {
         e = cudaMemcpy(host_dst, plan->pp.tb, (size_t)bytes, cudaMemcpyDeviceToHost);
         return e == cudaSuccess ? MSA_OK : cuda_error(e, "traceback tensor copy");
     }
-    // column-blocked device layout -> row-major host copy
     std::vector<uint8_t> dev((size_t)hp.tb_dev_bytes);
     e = cudaMemcpy(dev.data(), plan->pp.tb, dev.size(), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "traceback tensor copy");
     uint8_t *out = static_cast<uint8_t *>(host_dst);
+    if (hp.tb_layout == 2) {
+        // tile-major device layout -> row-major host copy, cell by cell
+        const int k = hp.k;
+        int64_t vol = 1;
+        for (int i = 0; i < k; ++i) vol *= hp.E[i];
+        int x[MSA_MAX_K] = {};
+        for (int64_t n = 0; n < hp.cells; ++n) {
+            int64_t dst = 0, t = 0, loc = 0;
+            for (int i = 0; i < k; ++i) {
+                dst += x[i] * hp.tbstride[i];
+                const int q = x[i] / hp.E[i];
+                t += q * hp.gstride[i];
+                loc = loc * hp.E[i] + (x[i] - q * hp.E[i]);
+            }
+            if (dst < bytes) out[dst] = dev[(size_t)(t * vol + loc)];
+            for (int i = k - 1; i >= 0; --i) {  // next cell in row-major order
+                if (++x[i] < hp.rho[i]) break;
+                x[i] = 0;
+            }
+        }
+        return MSA_OK;
+    }
+    // column-blocked device layout -> row-major host copy
     const int rho2 = hp.rho[2];
     const int64_t colb = c3::tb_col_bytes(rho2);
     for (int x0 = 0; x0 < hp.rho[0]; ++x0) {

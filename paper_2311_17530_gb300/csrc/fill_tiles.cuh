@@ -23,13 +23,24 @@ namespace msadp {
 // Shared memory: the intra-tile schedule (8 bytes per cell) and plane offsets
 // for the CTA, then per warp the halo'd score tile, the traceback tile and the
 // residue codes along each axis.
+// Tile-major mode (k >= kTileMajorMinK) adds per CTA the halo table (one 8-byte
+// entry per halo cell: its shared-memory offset, which lower neighbour tile
+// holds it, and its offset in that tile's block) and the write-back table (the
+// shared-memory offset of each interior cell), and per warp the element offsets
+// of the neighbour tiles' blocks.
+template <int K, int E>
+__host__ __device__ constexpr int tiles_tm_cta_bytes() {
+    return K >= kTileMajorMinK ? round_up((geo_volh(K, E) - geo_vol(K, E)) * 8, 16) + round_up(geo_vol(K, E) * 2, 16) : 0;
+}
 template <int K, int E>
 __host__ __device__ constexpr int tiles_warp_bytes() {
-    return round_up(geo_volh(K, E) * 4, 16) + round_up(geo_vol(K, E), 16) + round_up(geo_codes(K, E), 16);
+    return round_up(geo_volh(K, E) * 4, 16) + round_up(geo_vol(K, E), 16) + round_up(geo_codes(K, E), 16) +
+           (K >= kTileMajorMinK ? (1 << K) * 4 : 0);
 }
 template <int K, int E>
 __host__ __device__ constexpr int tiles_cta_fixed_bytes() {
-    return round_up(geo_vol(K, E) * 8, 16) + round_up(geo_planes(K, E) + 1, 4) * 4 + round_up(geo_planes(K, E), 4) * 4;
+    return round_up(geo_vol(K, E) * 8, 16) + round_up(geo_planes(K, E) + 1, 4) * 4 + round_up(geo_planes(K, E), 4) * 4 +
+           tiles_tm_cta_bytes<K, E>();
 }
 // Warps per CTA: up to 8 (4 for k > 5), as many as fit in 200 KB of shared memory.
 template <int K, int E>
@@ -38,6 +49,8 @@ struct TilesCfg {
     static constexpr int kFit = (200 * 1024 - tiles_cta_fixed_bytes<K, E>()) / tiles_warp_bytes<K, E>();
     static constexpr int WARPS = kFit < 1 ? 1 : (kFit > kMax ? kMax : kFit);
     static_assert(kFit >= 1, "tile does not fit in shared memory");
+    static_assert(K < kTileMajorMinK || round_up(geo_planes(K, E), 4) >= WARPS + 1,
+                  "plane scratch holds the halo-table scan");
     static_assert(geo_volh(K, E) < 65536 && geo_vol(K, E) < 65536, "schedule entries hold 16-bit offsets");
     static_assert(E < (K <= 4 ? 256 : 16) && tile_ext(K, E, K - 1) < (K <= 4 ? 256 : 16),
                   "packed local coordinates");
@@ -59,11 +72,17 @@ fill_tiles_kernel(const LaunchDesc L) {
     constexpr unsigned CMASK = (1u << CB) - 1;
     constexpr int MASKB = (1 << K) - 1;  // tie bits B = k
 
+    constexpr bool TM = K >= kTileMajorMinK;  // tile-major scratch and traceback
+    constexpr int NH = VOLH - VOL;            // halo cells
+
     extern __shared__ __align__(16) unsigned char smem[];
     uint2 *sched = reinterpret_cast<uint2 *>(smem);
     int *pstart = reinterpret_cast<int *>(smem + round_up(VOL * 8, 16));
     int *pcur = pstart + round_up(PLANES + 1, 4);
-    unsigned char *wbase = reinterpret_cast<unsigned char *>(pcur + round_up(PLANES, 4));
+    uint2 *htab = reinterpret_cast<uint2 *>(pcur + round_up(PLANES, 4));
+    uint16_t *wtab = reinterpret_cast<uint16_t *>(reinterpret_cast<unsigned char *>(htab) +
+                                                  (TM ? round_up(NH * 8, 16) : 0));
+    unsigned char *wbase = reinterpret_cast<unsigned char *>(htab) + tiles_tm_cta_bytes<K, E>();
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -107,9 +126,58 @@ fill_tiles_kernel(const LaunchDesc L) {
     }
     __syncthreads();
 
+    if constexpr (TM) {
+        // write-back table: the shared-memory offset of each interior cell (local row-major)
+        for (int i = tid; i < VOL; i += blockDim.x) {
+            int rem = i, soff = 0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const int c = rem / geo_st(K, E, j);
+                rem -= c * geo_st(K, E, j);
+                soff += (c + 1) * geo_sh(K, E, j);
+            }
+            wtab[i] = (uint16_t)soff;
+        }
+        // halo table, in shared-memory order: cells with some local coordinate -1
+        // belong to the lower neighbour tile S (the axes at -1), at local
+        // coordinate E - 1 on those axes. Ranked chunk by chunk with a block scan
+        // (pcur is free once the schedule is built: warp counts, then the running total).
+        const int nwarps = (int)(blockDim.x >> 5);
+        if (tid == 0) pcur[nwarps] = 0;
+        __syncthreads();
+        for (int base = 0; base < VOLH; base += blockDim.x) {
+            const int i = base + tid;
+            bool halo = false;
+            uint32_t S = 0, loff = 0;
+            if (i < VOLH) {
+                int rem = i;
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const int d = rem / geo_sh(K, E, j);  // halo'd coordinate 0 .. E_j
+                    rem -= d * geo_sh(K, E, j);
+                    const int cl = d == 0 ? tile_ext(K, E, j) - 1 : d - 1;
+                    if (d == 0) S |= 1u << j;
+                    loff += (uint32_t)(cl * geo_st(K, E, j));
+                }
+                halo = S != 0;
+            }
+            const unsigned bal = __ballot_sync(kFull, halo);
+            if (lane == 0) pcur[warp] = __popc(bal);
+            __syncthreads();
+            int pos = pcur[nwarps] + __popc(bal & ((1u << lane) - 1));
+            for (int w2 = 0; w2 < warp; ++w2) pos += pcur[w2];
+            if (halo) htab[pos] = make_uint2((uint32_t)i | (S << 16), loff);
+            __syncthreads();
+            if (tid == 0)
+                for (int w2 = 0; w2 < nwarps; ++w2) pcur[nwarps] += pcur[w2];
+            __syncthreads();
+        }
+    }
+
     int32_t *qs = reinterpret_cast<int32_t *>(wbase + warp * tiles_warp_bytes<K, E>());
     unsigned char *tbs = reinterpret_cast<unsigned char *>(qs) + round_up(VOLH * 4, 16);
     unsigned char *tcs = tbs + round_up(VOL, 16);
+    int *nbase = reinterpret_cast<int *>(tcs + round_up(geo_codes(K, E), 16));
 
     while (true) {
         int t = 0;
@@ -170,13 +238,46 @@ fill_tiles_kernel(const LaunchDesc L) {
                         (x >= 1 && x <= len[j]) ? codes[cofs[j] + x - 1] : (uint8_t)0;
                 }
 
-            // Halo: every cell with some local coordinate -1, face by face. Loads
-            // bypass L1 (other SMs wrote these cells) and are issued in batches of
-            // HB before their shared-memory stores, so a face costs about one L2
-            // round trip per batch rather than one per element.
+            // Halo: every cell with some local coordinate -1. Loads bypass L1
+            // (other SMs wrote these cells) and are issued in batches of HB before
+            // their shared-memory stores, so the halo costs about one L2 round trip
+            // per batch rather than one per element.
             constexpr int HB = 8;
+            if constexpr (TM) {
+                // lower neighbour tiles' blocks (none across the origin faces)
+                for (int S = lane + 1; S < (1 << K); S += 32) {
+                    int64_t nb = lin;
+                    bool ok = true;
 #pragma unroll
-            for (int f = 0; f < K; ++f) {
+                    for (int j = 0; j < K; ++j)
+                        if ((S >> j) & 1) {
+                            ok = ok && tco[j] > 0;
+                            nb -= P.gstride[j];
+                        }
+                    nbase[S] = ok ? (int)(nb * VOL) : -1;
+                }
+                __syncwarp();
+                for (int i0 = 0; i0 < NH; i0 += 32 * HB) {
+                    int val[HB], dst[HB];
+#pragma unroll
+                    for (int u = 0; u < HB; ++u) {
+                        const int i = i0 + 32 * u + lane;
+                        dst[u] = -1;
+                        val[u] = kNeg;
+                        if (i < NH) {
+                            const uint2 h = htab[i];
+                            const int b = nbase[h.x >> 16];
+                            dst[u] = (int)(h.x & 0xFFFFu);
+                            if (b >= 0) val[u] = __ldcg(Qg + b + h.y);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < HB; ++u)
+                        if (dst[u] >= 0) qs[dst[u]] = val[u];
+                }
+            }
+#pragma unroll
+            for (int f = 0; f < (TM ? 0 : K); ++f) {
                 for (int i0 = 0; i0 < face_size(K, E, f); i0 += 32 * HB) {
                     int val[HB], dst[HB];
 #pragma unroll
@@ -269,7 +370,16 @@ fill_tiles_kernel(const LaunchDesc L) {
             // Write back scores (for successor halos) and traceback bytes.
             int32_t *__restrict__ Qw = P.Q;
             uint8_t *__restrict__ tbw = P.tb;
-            for (int i = lane; i < VOL; i += 32) {
+            if constexpr (TM) {
+                // this tile's blocks, contiguous (cells outside the tensor included)
+                int32_t *qb = Qw + lin * VOL;
+                uint8_t *tbb = tbw + lin * VOL;
+                for (int i = lane; i < VOL; i += 32) {
+                    qb[i] = qs[wtab[i]];
+                    tbb[i] = tbs[i];
+                }
+            }
+            for (int i = lane; i < (TM ? 0 : VOL); i += 32) {
                 int r = i, soff = 0;
                 bool in = true;
                 int64_t gq = 0, gt = 0;

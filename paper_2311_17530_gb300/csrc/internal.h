@@ -52,7 +52,7 @@ struct ProblemDesc {
     int64_t face1_stride;        // column kernel: ints per column in aux (axis-1 faces)
     int32_t face0_rows;          // column kernel: skewed rows per axis-0 face
     int32_t face1_rows;          // column kernel: skewed rows per axis-1 face
-    int32_t tb_layout;           // 0: row-major (tbstride); 1: column-blocked (column kernel)
+    int32_t tb_layout;           // 0: row-major (tbstride); 1: column-blocked (column kernel); 2: tile-major
     int32_t pad3;
     const uint8_t *amap;         // device 256-entry char -> code map (0xFF: invalid)
     uint8_t *codes;              // device codes
@@ -97,6 +97,10 @@ struct LaunchDesc {
 // until it has); the kernel is instantiated per (k, E).
 __host__ __device__ constexpr int tile_ext(int k, int edge, int i) { return k == 2 && i == 1 ? 2 * edge : edge; }
 constexpr int kMaxTileEdges = 3;
+// From this k on the generic kernel keeps its score scratch and traceback bytes
+// tile-major (each tile one contiguous block), so halo reads and write-back are
+// block transfers.
+constexpr int kTileMajorMinK = 4;
 // candidate edges per k (0 = unused slot)
 __host__ __device__ constexpr int tile_edge_candidate(int k, int idx) {
     return k == 2 ? (idx == 0 ? 16 : idx == 1 ? 32 : 64)

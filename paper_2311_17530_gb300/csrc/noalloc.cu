@@ -104,19 +104,8 @@ int noalloc_plan(int k, const int32_t *lens, int A, HostPlan &hp) {
     }
     hp.ntiles = nt;
     hp.waves = gsum - k + 1;
-    int64_t s = 1;
-    for (int i = k - 1; i >= 0; --i) {
-        hp.qstride[i] = s;
-        s *= (i == k - 1) ? (hp.rho[i] + 3) / 4 * 4 : hp.rho[i];
-    }
-    hp.qelems = s;
-    s = 1;
-    for (int i = k - 1; i >= 0; --i) {
-        hp.tbstride[i] = s;
-        s *= (i == k - 1) ? (hp.rho[i] + kTbRowAlign - 1) / kTbRowAlign * kTbRowAlign : hp.rho[i];
-    }
-    hp.tbbytes = s;
-    hp.tb_dev_bytes = s;
+    if (!score_and_traceback_layout(hp))
+        return set_error(MSA_ETOOBIG, "msa_align_noalloc: score scratch beyond 32-bit offsets");
     return MSA_OK;
 }
 

@@ -79,6 +79,38 @@ void wave_sizes(int k, const int32_t *grid, std::vector<int64_t> &out) {
 
 static int64_t round_up64(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+bool score_and_traceback_layout(HostPlan &hp) {
+    const int k = hp.k;
+    // score scratch: full tensor, last axis padded to 4 elements (16-byte rows)
+    int64_t s = 1;
+    for (int i = k - 1; i >= 0; --i) {
+        hp.qstride[i] = s;
+        s *= (i == k - 1) ? round_up64(hp.rho[i], 4) : hp.rho[i];
+    }
+    hp.qelems = s;
+    // traceback tensor (row-major view, the layout msa_plan_read_tb returns):
+    // last axis padded to 16-byte rows
+    s = 1;
+    for (int i = k - 1; i >= 0; --i) {
+        hp.tbstride[i] = s;
+        s *= (i == k - 1) ? round_up64(hp.rho[i], kTbRowAlign) : hp.rho[i];
+    }
+    hp.tbbytes = s;
+    hp.tb_layout = 0;
+    hp.tb_dev_bytes = hp.tbbytes;
+    if (hp.kernel == kKernelTiles && k >= kTileMajorMinK) {
+        // tile-major scratch and traceback on the device: tile t's cells form one
+        // block of prod(E_i) entries in local row-major order (edge tiles padded)
+        int64_t vol = 1;
+        for (int i = 0; i < k; ++i) vol *= hp.E[i];
+        if (hp.ntiles * vol >= (1LL << 31)) return false;
+        hp.qelems = hp.ntiles * vol;
+        hp.tb_layout = 2;
+        hp.tb_dev_bytes = hp.ntiles * vol;
+    }
+    return true;
+}
+
 int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err, int edge) {
     char buf[256];
     if (k < 2 || k > MSA_MAX_K) {
@@ -148,22 +180,10 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
     for (int i = 0; i < k; ++i) gsum += hp.G[i];
     hp.waves = gsum - k + 1;
 
-    // score scratch: full tensor, last axis padded to 4 elements (16-byte rows)
-    int64_t s = 1;
-    for (int i = k - 1; i >= 0; --i) {
-        hp.qstride[i] = s;
-        s *= (i == k - 1) ? round_up64(hp.rho[i], 4) : hp.rho[i];
+    if (!score_and_traceback_layout(hp)) {
+        err = "score scratch beyond 32-bit element offsets";
+        return MSA_ETOOBIG;
     }
-    hp.qelems = s;
-    // traceback tensor: row-major, last axis padded to 16-byte rows
-    s = 1;
-    for (int i = k - 1; i >= 0; --i) {
-        hp.tbstride[i] = s;
-        s *= (i == k - 1) ? round_up64(hp.rho[i], kTbRowAlign) : hp.rho[i];
-    }
-    hp.tbbytes = s;
-    hp.tb_layout = 0;
-    hp.tb_dev_bytes = hp.tbbytes;
 
     if (hp.kernel == kKernelCol3) {
         // faces between columns and the column order: a column (a, b) can start

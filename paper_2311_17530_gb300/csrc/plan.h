@@ -33,7 +33,7 @@ struct HostPlan {
     int32_t face1_rows = 0;
     int64_t tbstride[MSA_MAX_K] = {};  // row-major strides (the layout msa_plan_read_tb returns)
     int64_t tbbytes = 0;               // row-major size
-    int32_t tb_layout = 0;             // device layout: 0 row-major, 1 column-blocked
+    int32_t tb_layout = 0;             // device layout: 0 row-major, 1 column-blocked, 2 tile-major
     int64_t tb_dev_bytes = 0;          // device size of the traceback tensor
     int32_t edge = 0;              // tile edge of the generic kernel (tile_ext), 0 for the column kernel
     int32_t pair_min_sum = 0;
@@ -52,6 +52,11 @@ int tile_edge_for(int k);
 int set_tile_edge(int k, int edge);
 bool prefer_tiles_k3();
 void set_prefer_tiles_k3(bool v);
+
+// Score scratch and traceback layouts from k, rho, the kernel, tile extents and
+// tile count (row-major, or tile-major for the generic kernel at k >= 4).
+// False when the scratch would need offsets beyond 32 bits.
+bool score_and_traceback_layout(HostPlan &hp);
 
 // Fill `hp` for one problem. Returns MSA_OK or an MSA_E* code with `err` set.
 // edge < 0 takes the current tuned edge for k.

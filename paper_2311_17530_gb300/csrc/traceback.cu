@@ -9,7 +9,7 @@
 //     so a window holds at least kTbcT / 3 moves unless the walk leaves the column;
 //   * row-major layout, k <= 3: boxes [x - D, x] (rows of the last axis copied in
 //     16-byte granules);
-//   * row-major layout, k >= 4 (short paths, large boxes): no staging; warp 0
+//   * k >= 4 (row-major or tile-major; short paths, large boxes): no staging; warp 0
 //     loads the traceback bytes of the current cell and of all its predecessors
 //     in one round trip, which fixes two moves.
 // The walk records only the masks (last column first). The score is computed
@@ -163,7 +163,26 @@ __device__ void walk_boxes(const ProblemDesc &P, const IODesc &io, unsigned char
     }
 }
 
-// Row-major layout, k >= 4: the current cell and all its predecessors per round trip.
+// Byte offset of cell x in the traceback tensor: row-major (tbstride), or
+// tile-major (layout 2: tile t = sum (x_i / E_i) gstride_i holds a block of
+// prod E_i bytes in local row-major order).
+__device__ __forceinline__ int64_t tb_cell(const ProblemDesc &P, const int *x, int64_t vol) {
+    int64_t g = 0;
+    if (P.tb_layout == 2) {
+        int64_t t = 0, loc = 0;
+        for (int i = 0; i < P.k; ++i) {
+            const int e = P.E[i], q = x[i] / e;
+            t += (int64_t)q * P.gstride[i];
+            loc = loc * e + (x[i] - q * e);
+        }
+        g = t * vol + loc;
+    } else {
+        for (int i = 0; i < P.k; ++i) g += (int64_t)x[i] * P.tbstride[i];
+    }
+    return g;
+}
+
+// k >= 4 (row-major or tile-major): the current cell and all its predecessors per round trip.
 __device__ void walk_direct(const ProblemDesc &P, const IODesc &io, unsigned char *pred, WalkState &ws) {
     const int tid = threadIdx.x;
     const int K = P.k;
@@ -171,18 +190,19 @@ __device__ void walk_direct(const ProblemDesc &P, const IODesc &io, unsigned cha
     if (tid >= 32) return;
     int x[MSA_MAX_K];
     for (int i = 0; i < K; ++i) x[i] = ws.x[i];
+    int64_t vol = 1;
+    for (int i = 0; i < K; ++i) vol *= P.E[i];
     int ncols = 0, fail = 0;
     while (!fail && !at_origin(K, x)) {
         // slot 0: the cell itself; slot m: its predecessor x - e_m (if inside)
         for (int m = tid; m <= NM; m += 32) {
-            int64_t g = 0;
+            int c[MSA_MAX_K];
             bool in = true;
             for (int i = 0; i < K; ++i) {
-                const int c = x[i] - ((m >> i) & 1);
-                in = in && c >= 0;
-                g += (int64_t)c * P.tbstride[i];
+                c[i] = x[i] - ((m >> i) & 1);
+                in = in && c[i] >= 0;
             }
-            pred[m] = in ? __ldcg(P.tb + g) : (unsigned char)0;
+            pred[m] = in ? __ldcg(P.tb + tb_cell(P, c, vol)) : (unsigned char)0;
         }
         __syncwarp();
         if (tid == 0) {
