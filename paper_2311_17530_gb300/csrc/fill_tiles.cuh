@@ -32,11 +32,18 @@ template <int K, int E>
 __host__ __device__ constexpr int tiles_tm_cta_bytes() {
     return K >= kTileMajorMinK ? round_up((geo_volh(K, E) - geo_vol(K, E)) * 8, 16) + round_up(geo_vol(K, E) * 2, 16) : 0;
 }
+// pair tables of a tile (k >= kTileMajorMinK): for each pair l < h of sequences,
+// the scaled pair score of every local coordinate pair (a, b), E x E entries
+template <int K, int E>
+__host__ __device__ constexpr int tiles_ptab_ints() {
+    return K >= kTileMajorMinK ? K * (K - 1) / 2 * E * E : 0;
+}
 template <int K, int E>
 __host__ __device__ constexpr int tiles_warp_bytes() {
     return round_up(geo_volh(K, E) * 4, 16) + round_up(geo_vol(K, E), 16) + round_up(geo_codes(K, E), 16) +
-           (K >= kTileMajorMinK ? (1 << K) * 4 : 0);
+           (K >= kTileMajorMinK ? (1 << K) * 4 + round_up(tiles_ptab_ints<K, E>() * 4, 16) : 0);
 }
+__host__ __device__ constexpr int pair_index(int K, int l, int h) { return l * K - l * (l + 1) / 2 + (h - l - 1); }
 template <int K, int E>
 __host__ __device__ constexpr int tiles_cta_fixed_bytes() {
     return round_up(geo_vol(K, E) * 8, 16) + round_up(geo_planes(K, E) + 1, 4) * 4 + round_up(geo_planes(K, E), 4) * 4 +
@@ -110,20 +117,33 @@ fill_tiles_kernel(const LaunchDesc L) {
         pstart[PLANES] = acc;
     }
     __syncthreads();
-    for (int i = tid; i < VOL; i += blockDim.x) {
-        int s = 0, rem = i, soff = 0;
-        uint32_t pk = 0;
+    // placement by one warp, 32 cells at a time in index order, so every plane
+    // lists its cells in increasing local index (neighbouring lanes then read
+    // nearby shared-memory words)
+    if (warp == 0)
+        for (int i0 = 0; i0 < VOL; i0 += 32) {
+            const int i = i0 + lane;
+            int s = 0, rem = i, soff = 0;
+            uint32_t pk = 0;
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const int c = rem / geo_st(K, E, j);
-            rem -= c * geo_st(K, E, j);
-            s += c;
-            soff += (c + 1) * geo_sh(K, E, j);
-            pk |= (uint32_t)c << (CB * j);
+            for (int j = 0; j < K; ++j) {
+                const int c = rem / geo_st(K, E, j);
+                rem -= c * geo_st(K, E, j);
+                s += c;
+                soff += (c + 1) * geo_sh(K, E, j);
+                pk |= (uint32_t)c << (CB * j);
+            }
+            const bool live = i < VOL;
+            const unsigned act = __ballot_sync(kFull, live);
+            const unsigned same = __match_any_sync(kFull, live ? s : -1);
+            if (live) {
+                const int pos = pcur[s] + __popc(same & ((1u << lane) - 1));
+                sched[pos] = make_uint2((uint32_t)soff | ((uint32_t)i << 16), pk);
+            }
+            __syncwarp();
+            if (live && lane == __ffs(same & act) - 1) pcur[s] += __popc(same);
+            __syncwarp();
         }
-        const int pos = atomicAdd(&pcur[s], 1);
-        sched[pos] = make_uint2((uint32_t)soff | ((uint32_t)i << 16), pk);
-    }
     __syncthreads();
 
     if constexpr (TM) {
@@ -178,6 +198,7 @@ fill_tiles_kernel(const LaunchDesc L) {
     unsigned char *tbs = reinterpret_cast<unsigned char *>(qs) + round_up(VOLH * 4, 16);
     unsigned char *tcs = tbs + round_up(VOL, 16);
     int *nbase = reinterpret_cast<int *>(tcs + round_up(geo_codes(K, E), 16));
+    int *ptab = nbase + (TM ? (1 << K) : 0);
 
     while (true) {
         int t = 0;
@@ -237,6 +258,22 @@ fill_tiles_kernel(const LaunchDesc L) {
                     tcs[geo_code_base(K, E, j) + c] =
                         (x >= 1 && x <= len[j]) ? codes[cofs[j] + x - 1] : (uint8_t)0;
                 }
+
+            if constexpr (TM) {
+                // this tile's pair tables: ptab[pair(l,h)][a*E + b] = tab[code_l(a)][code_h(b)]
+                __syncwarp();
+                for (int idx = lane; idx < tiles_ptab_ints<K, E>(); idx += 32) {
+                    const int pr = idx / (E * E), ab = idx - pr * (E * E);
+                    int l = 0, rest = pr;
+                    while (rest >= K - 1 - l) {
+                        rest -= K - 1 - l;
+                        ++l;
+                    }
+                    const int h = l + 1 + rest;
+                    const int ca = tcs[geo_code_base(K, E, l) + ab / E], cb = tcs[geo_code_base(K, E, h) + ab % E];
+                    ptab[idx] = __ldg(tab + ca * A + cb);
+                }
+            }
 
             // Halo: every cell with some local coordinate -1. Loads bypass L1
             // (other SMs wrote these cells) and are issued in batches of HB before
@@ -331,8 +368,10 @@ fill_tiles_kernel(const LaunchDesc L) {
                         continue;
                     }
                     int a[K];
+                    if constexpr (!TM) {
 #pragma unroll
-                    for (int j = 0; j < K; ++j) a[j] = tcs[geo_code_base(K, E, j) + c[j]];
+                        for (int j = 0; j < K; ++j) a[j] = tcs[geo_code_base(K, E, j) + c[j]];
+                    }
                     // Candidates grouped by the move's highest sequence h. The pair
                     // sum of m = r | 2^h is S[r] + T[r] with T[r] = sum_{l in r}
                     // (scaled pair l, h); S is stored only below 2^(K-1), the top
@@ -348,7 +387,12 @@ fill_tiles_kernel(const LaunchDesc L) {
                     for (int h = 1; h < K; ++h) {
                         int ph[K];
 #pragma unroll
-                        for (int l = 0; l < h; ++l) ph[l] = __ldg(tab + a[l] * A + a[h]);
+                        for (int l = 0; l < h; ++l) {
+                            if constexpr (TM)
+                                ph[l] = ptab[pair_index(K, l, h) * (E * E) + c[l] * E + c[h]];
+                            else
+                                ph[l] = __ldg(tab + a[l] * A + a[h]);
+                        }
                         int T[1 << (K - 1)];
                         T[0] = 0;
 #pragma unroll
