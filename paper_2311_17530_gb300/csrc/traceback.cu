@@ -72,12 +72,20 @@ __device__ void walk_col3(const ProblemDesc &P, const IODesc &io, unsigned char 
         const int cA = x0 / c3::WR, cB = x1 >> 5;
         const int t_lo = x2 + (x1 & 31) + x0 % c3::WR - (kTbcT - 1);
         const unsigned char *col = P.tb + (int64_t)(cA * NB + cB) * colb;
-        // window rows: CTA times [t_lo, t_lo + kTbcT), all warp blocks and lanes (1024 B per time)
-        for (int i = tid; i < kTbcBytes / 16; i += kTbThreads) {
-            const int tt = t_lo + i / (c3::W * 32 * c3::R / 16);
+        // window: CTA times [t_lo, t_lo + kTbcT); the walk only moves to lower
+        // rows and lanes, so only warp blocks 0 .. w and lanes 0 .. l of each time
+        // are staged (16-byte runs from the start of each warp block's 32 * R bytes)
+        constexpr int kRowB = 32 * c3::R;                              // bytes per (time, warp block)
+        const int nw = x0 % c3::WR / c3::R + 1;                        // warp blocks staged
+        const int ncp = ((x1 & 31) * c3::R + c3::R + 15) / 16;         // 16-byte runs per warp block
+        const int per_t = nw * ncp;
+        for (int i = tid; i < kTbcT * per_t; i += kTbThreads) {
+            const int row = i / per_t, rem = i - row * per_t;
+            const int w = rem / ncp, part = rem - w * ncp;
+            const int tt = t_lo + row;
             if (tt >= 0 && tt < nT)
-                cp_async_16(win + 16 * i, col + (int64_t)(tt + c3::U) * (c3::W * 32 * c3::R) +
-                                              16 * (i % (c3::W * 32 * c3::R / 16)));
+                cp_async_16(win + (row * c3::W + w) * kRowB + 16 * part,
+                            col + (int64_t)(tt + c3::U) * (c3::W * kRowB) + w * kRowB + 16 * part);
         }
         cp_async_wait_all();
         __syncthreads();
