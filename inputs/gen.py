@@ -67,6 +67,23 @@ def dna_table(match: int = 5, mismatch: int = -4) -> np.ndarray:
     return t
 
 
+# The scoring the paper reports its similarity scores with (section 5.2): +1 for
+# a match, 0 for a mismatch, -1 for a residue against a gap (gap/gap pairs 0).
+PAPER_GAP = -1
+
+
+def paper_table(size: int) -> np.ndarray:
+    """Match +1 / mismatch 0 over an alphabet of ``size`` letters."""
+    return np.eye(size, dtype=np.int32)
+
+
+def paper_problem(seed: int, k: int, lens: List[int], alphabet: str = DNA, related: bool = True) -> Problem:
+    """A seeded problem scored with the paper's +1/0/-1/0 scheme."""
+    p = random_problem(seed, k, lens, alphabet=alphabet, table=paper_table(len(alphabet)), gap=PAPER_GAP,
+                       related=related)
+    return Problem(f"paper_s{seed}_k{k}_{'x'.join(map(str, lens))}", p.seqs, alphabet, p.subst, PAPER_GAP, seed)
+
+
 def protein_table(rng: np.random.Generator, size: int = 20) -> np.ndarray:
     """Symmetric table: diagonal U[4,11], off-diagonal U[-4,3] (inclusive)."""
     t = np.zeros((size, size), dtype=np.int32)

@@ -172,3 +172,24 @@ def test_empty_sequences():
     # k=3 with one empty row: each column also pays one residue/gap pair per residue
     r = oracle.align(["ACG", "", "AG"], "ACGT", t, -8)
     assert rescore_rows(r.rows, "ACGT", t, -8) == r.score
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_paper_scheme_brute_force(k):
+    """The paper's +1/0/-1/0 scoring (section 5.2) against exhaustive enumeration."""
+    rng = np.random.default_rng(40 + k)
+    lens = [int(x) for x in rng.integers(0, 4 if k < 4 else 3, size=k)]
+    seqs = [inputs.random_seq(rng, "ACGT", n) for n in lens]
+    table = inputs.paper_table(4)
+    bs, bm = brute_force(seqs, "ACGT", table, inputs.PAPER_GAP)
+    r = oracle.align(seqs, "ACGT", table, inputs.PAPER_GAP)
+    assert (r.score, r.masks) == (bs, bm)
+
+
+@pytest.mark.parametrize("k", [7, 8])
+def test_paper_scheme_identical_sequences_closed_form(k):
+    """k copies of one sequence under +1/0/-1/0: C(k,2) * L, all-diagonal."""
+    s = "ACGTTGCA"[: 9 - k]
+    r = oracle.align([s] * k, "ACGT", inputs.paper_table(4), inputs.PAPER_GAP)
+    assert r.score == k * (k - 1) // 2 * len(s)
+    assert r.masks == [(1 << k) - 1] * len(s)
