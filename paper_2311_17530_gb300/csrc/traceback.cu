@@ -3,10 +3,12 @@
 //
 // One CTA of 256 threads per problem. The walk is a chain of dependent reads, so
 // thread 0 walks; the rest of the CTA stages the data it reads:
-//   * column layout (k = 3 column kernel): windows of kTbcT CTA times x every
-//     warp block x every lane of one column (64 KB, cp.async by all threads);
-//     every move lowers the CTA time T = x2 + l + (x0 mod WR) by its popcount,
-//     so a window holds at least kTbcT / 3 moves unless the walk leaves the column;
+//   * column layout (k = 3 column kernel): windows of one column, as many CTA
+//     times as fit in shared memory of the warp blocks and lanes the walk can
+//     still reach (cp.async by all threads), for about as many CTA times as a
+//     diagonal walk needs to leave the column; every move lowers the CTA time
+//     T = x2 + l + (x0 mod WR) by its popcount, so a window of n times holds at
+//     least n / 3 moves unless the walk leaves the column;
 //   * row-major layout, k <= 3: boxes [x - D, x] (rows of the last axis copied in
 //     16-byte granules);
 //   * k >= 4 (row-major or tile-major; short paths, large boxes): no staging; warp 0
@@ -25,9 +27,7 @@ namespace msadp {
 namespace {
 
 constexpr int kTbThreads = 256;
-constexpr int kTbcT = 64;                                   // CTA times per column window
-constexpr int kTbcBytes = kTbcT * c3::W * 32 * c3::R;       // 64 KB
-static_assert(kTbcBytes <= kTracebackSmem, "traceback window exceeds its shared memory");
+static_assert(c3::W * 32 * c3::R <= kTracebackSmem, "a traceback window holds at least one CTA time");
 
 __device__ __forceinline__ void cp_async_16(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -70,22 +70,26 @@ __device__ void walk_col3(const ProblemDesc &P, const IODesc &io, unsigned char 
         if (ws.fail || at_origin(3, ws.x)) break;
         const int x0 = ws.x[0], x1 = ws.x[1], x2 = ws.x[2];
         const int cA = x0 / c3::WR, cB = x1 >> 5;
-        const int t_lo = x2 + (x1 & 31) + x0 % c3::WR - (kTbcT - 1);
         const unsigned char *col = P.tb + (int64_t)(cA * NB + cB) * colb;
-        // window: CTA times [t_lo, t_lo + kTbcT); the walk only moves to lower
-        // rows and lanes, so only warp blocks 0 .. w and lanes 0 .. l of each time
-        // are staged (16-byte runs from the start of each warp block's 32 * R bytes)
+        // window: the walk only moves to lower rows and lanes, so only warp blocks
+        // 0 .. w and lanes 0 .. l are staged (16-byte runs from the start of each
+        // warp block's 32 * R bytes), for as many CTA times as the shared memory
+        // holds (up to 255): [t_hi - nt + 1, t_hi]
         constexpr int kRowB = 32 * c3::R;                              // bytes per (time, warp block)
         const int nw = x0 % c3::WR / c3::R + 1;                        // warp blocks staged
         const int ncp = ((x1 & 31) * c3::R + c3::R + 15) / 16;         // 16-byte runs per warp block
-        const int per_t = nw * ncp;
-        for (int i = tid; i < kTbcT * per_t; i += kTbThreads) {
+        const int per_t = nw * ncp;                                    // runs per CTA time
+        // mostly diagonal paths leave the column after about min(row, lane) moves
+        // of three CTA times each: stage that much (plus slack), within the memory
+        const int nt = min(min(255, kTracebackSmem / (16 * per_t)), 3 * min(x0 % c3::WR, x1 & 31) + 24);
+        const int t_hi = x2 + (x1 & 31) + x0 % c3::WR;
+        const int t_lo = t_hi - nt + 1;
+        for (int i = tid; i < nt * per_t; i += kTbThreads) {
             const int row = i / per_t, rem = i - row * per_t;
             const int w = rem / ncp, part = rem - w * ncp;
             const int tt = t_lo + row;
             if (tt >= 0 && tt < nT)
-                cp_async_16(win + (row * c3::W + w) * kRowB + 16 * part,
-                            col + (int64_t)(tt + c3::U) * (c3::W * kRowB) + w * kRowB + 16 * part);
+                cp_async_16(win + 16 * i, col + (int64_t)(tt + c3::U) * (c3::W * kRowB) + w * kRowB + 16 * part);
         }
         cp_async_wait_all();
         __syncthreads();
@@ -96,7 +100,8 @@ __device__ void walk_col3(const ProblemDesc &P, const IODesc &io, unsigned char 
                 const int rho = x[0] % c3::WR, l = x[1] & 31;
                 const int tt = x[2] + l + rho;
                 if (x[0] / c3::WR != cA || (x[1] >> 5) != cB || tt < t_lo) break;
-                const int m = win[((tt - t_lo) * c3::W + rho / c3::R) * (32 * c3::R) + l * c3::R + rho % c3::R];
+                const int byte = l * c3::R + rho % c3::R;  // < ncp * 16: l and rho only decrease in a column
+                const int m = win[((tt - t_lo) * nw + rho / c3::R) * (16 * ncp) + byte];
                 if (!take_move(3, m, x, P, io, ws.ncols)) {
                     ws.fail = 1;
                     break;
