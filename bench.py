@@ -344,8 +344,12 @@ def run_gb300(args, rank, world, local):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     p = inputs.WORKLOADS[args.workload]()
     total_len = sum(p.lens)
-    # the autotuner picks the tile shape (and for k = 3 the kernel) for this shape
-    tuning = None if args.no_autotune else msadp.msa_autotune(p.lens, len(p.alphabet), repeats=2)
+    # the autotuner picks the tile shape (and for k = 3 the kernel) for this shape,
+    # unless a tile edge is given
+    if args.tile_edge:
+        msadp.msa_set_tile_edge(p.k, args.tile_edge)
+        msadp.msa_config("fill_kernel", 1)
+    tuning = None if (args.no_autotune or args.tile_edge) else msadp.msa_autotune(p.lens, len(p.alphabet), repeats=2)
     plan = msadp.Plan(p.k, p.lens, p.alphabet)
     info = plan.info()
     d_res, d_sub = msadp.device_inputs(p, dev)
@@ -462,6 +466,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
+    ap.add_argument("--tile-edge", type=int, default=0, help="generic tile kernel with this tile edge")
     ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving stream")
     ap.add_argument("--cpu-cells", type=float, default=1.2e8, help="cells of the cpu_baseline sample")
     ap.add_argument("--ref-cells", type=float, default=5e7, help="cells per step of --impl reference")

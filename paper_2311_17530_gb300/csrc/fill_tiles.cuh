@@ -28,9 +28,22 @@ namespace msadp {
 // holds it, and its offset in that tile's block) and the write-back table (the
 // shared-memory offset of each interior cell), and per warp the element offsets
 // of the neighbour tiles' blocks.
+// Halo entries pack (shared-memory offset, neighbour mask, offset in the
+// neighbour's block) into 4 bytes when the three fields fit, else 8.
+__host__ __device__ constexpr int bits_for(int n) {  // bits to hold 0 .. n - 1
+    int b = 0;
+    while ((1 << b) < n) ++b;
+    return b;
+}
+template <int K, int E>
+__host__ __device__ constexpr bool tiles_halo_packed() {
+    return bits_for(geo_volh(K, E)) + K + bits_for(geo_vol(K, E)) <= 32;
+}
 template <int K, int E>
 __host__ __device__ constexpr int tiles_tm_cta_bytes() {
-    return K >= kTileMajorMinK ? round_up((geo_volh(K, E) - geo_vol(K, E)) * 8, 16) + round_up(geo_vol(K, E) * 2, 16) : 0;
+    return K >= kTileMajorMinK ? round_up((geo_volh(K, E) - geo_vol(K, E)) * (tiles_halo_packed<K, E>() ? 4 : 8), 16) +
+                                     round_up(geo_vol(K, E) * 2, 16)
+                               : 0;
 }
 // pair tables of a tile (k >= kTileMajorMinK): for each pair l < h of sequences,
 // the scaled pair score of every local coordinate pair (a, b), E x E entries
@@ -49,12 +62,31 @@ __host__ __device__ constexpr int tiles_cta_fixed_bytes() {
     return round_up(geo_vol(K, E) * 8, 16) + round_up(geo_planes(K, E) + 1, 4) * 4 + round_up(geo_planes(K, E), 4) * 4 +
            tiles_tm_cta_bytes<K, E>();
 }
-// Warps per CTA: up to 8 (4 for k > 5), as many as fit in 200 KB of shared memory.
+// Warps per CTA: the count (up to 8, 4 for k > 5) that keeps the most warps
+// resident per SM within its shared memory (227 KB per CTA, 228 KB per SM,
+// 1 KB reserved per CTA), preferring fewer warps per CTA on ties.
+constexpr int kSmemPerSm = 228 * 1024, kSmemPerCta = 227 * 1024, kSmemReservedPerCta = 1024;
+template <int K, int E>
+__host__ __device__ constexpr int tiles_best_warps(int kmax) {
+    int best = 1, best_res = 0;
+    for (int w = 1; w <= kmax; ++w) {
+        const int bytes = tiles_cta_fixed_bytes<K, E>() + w * tiles_warp_bytes<K, E>();
+        if (bytes > kSmemPerCta) break;
+        int ctas = kSmemPerSm / (bytes + kSmemReservedPerCta);
+        if (ctas > 32) ctas = 32;
+        const int resident = ctas * w > 48 ? 48 : ctas * w;  // warps per SM are capped by the hardware
+        if (resident > best_res) {
+            best_res = resident;
+            best = w;
+        }
+    }
+    return best;
+}
 template <int K, int E>
 struct TilesCfg {
-    static constexpr int kMax = K <= 5 ? 8 : 4;
-    static constexpr int kFit = (200 * 1024 - tiles_cta_fixed_bytes<K, E>()) / tiles_warp_bytes<K, E>();
-    static constexpr int WARPS = kFit < 1 ? 1 : (kFit > kMax ? kMax : kFit);
+    static constexpr int kMax = 8;
+    static constexpr int kFit = (kSmemPerCta - tiles_cta_fixed_bytes<K, E>()) / tiles_warp_bytes<K, E>();
+    static constexpr int WARPS = tiles_best_warps<K, E>(kMax);
     static_assert(kFit >= 1, "tile does not fit in shared memory");
     static_assert(K < kTileMajorMinK || round_up(geo_planes(K, E), 4) >= WARPS + 1,
                   "plane scratch holds the halo-table scan");
@@ -86,9 +118,12 @@ fill_tiles_kernel(const LaunchDesc L) {
     uint2 *sched = reinterpret_cast<uint2 *>(smem);
     int *pstart = reinterpret_cast<int *>(smem + round_up(VOL * 8, 16));
     int *pcur = pstart + round_up(PLANES + 1, 4);
+    constexpr bool HPK = tiles_halo_packed<K, E>();  // 4-byte halo entries
+    constexpr int SB = bits_for(VOLH), LB = bits_for(VOL);
     uint2 *htab = reinterpret_cast<uint2 *>(pcur + round_up(PLANES, 4));
+    uint32_t *htab4 = reinterpret_cast<uint32_t *>(htab);
     uint16_t *wtab = reinterpret_cast<uint16_t *>(reinterpret_cast<unsigned char *>(htab) +
-                                                  (TM ? round_up(NH * 8, 16) : 0));
+                                                  (TM ? round_up(NH * (HPK ? 4 : 8), 16) : 0));
     unsigned char *wbase = reinterpret_cast<unsigned char *>(htab) + tiles_tm_cta_bytes<K, E>();
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -186,7 +221,12 @@ fill_tiles_kernel(const LaunchDesc L) {
             __syncthreads();
             int pos = pcur[nwarps] + __popc(bal & ((1u << lane) - 1));
             for (int w2 = 0; w2 < warp; ++w2) pos += pcur[w2];
-            if (halo) htab[pos] = make_uint2((uint32_t)i | (S << 16), loff);
+            if (halo) {
+                if constexpr (HPK)
+                    htab4[pos] = (uint32_t)i | (S << SB) | (loff << (SB + K));
+                else
+                    htab[pos] = make_uint2((uint32_t)i | (S << 16), loff);
+            }
             __syncthreads();
             if (tid == 0)
                 for (int w2 = 0; w2 < nwarps; ++w2) pcur[nwarps] += pcur[w2];
@@ -302,10 +342,21 @@ fill_tiles_kernel(const LaunchDesc L) {
                         dst[u] = -1;
                         val[u] = kNeg;
                         if (i < NH) {
-                            const uint2 h = htab[i];
-                            const int b = nbase[h.x >> 16];
-                            dst[u] = (int)(h.x & 0xFFFFu);
-                            if (b >= 0) val[u] = __ldcg(Qg + b + h.y);
+                            int so, sm, lo;
+                            if constexpr (HPK) {
+                                const uint32_t h = htab4[i];
+                                so = (int)(h & ((1u << SB) - 1));
+                                sm = (int)((h >> SB) & ((1u << K) - 1));
+                                lo = (int)(h >> (SB + K));
+                            } else {
+                                const uint2 h = htab[i];
+                                so = (int)(h.x & 0xFFFFu);
+                                sm = (int)(h.x >> 16);
+                                lo = (int)h.y;
+                            }
+                            const int b = nbase[sm];
+                            dst[u] = so;
+                            if (b >= 0) val[u] = __ldcg(Qg + b + lo);
                         }
                     }
 #pragma unroll
