@@ -253,7 +253,7 @@ fill_tiles_kernel(const LaunchDesc L) {
         int o[K], e[K], tco[K], len[K], cofs[K];
         int64_t qstr[K], tstr[K];
         int64_t rem = lin;
-        bool corner = true, origin = true;
+        bool corner = true, origin = true, full = true;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const int64_t gs = P.gstride[j];
@@ -263,6 +263,7 @@ fill_tiles_kernel(const LaunchDesc L) {
             const int rho = P.rho[j];
             e[j] = min(tile_ext(K, E, j), rho - o[j]);
             corner = corner && (o[j] + e[j] == rho);
+            full = full && e[j] == tile_ext(K, E, j);
             origin = origin && (o[j] == 0);
             len[j] = P.len[j];
             cofs[j] = P.cofs[j];
@@ -405,14 +406,17 @@ fill_tiles_kernel(const LaunchDesc L) {
                     const uint2 sc = sched[idx];
                     const int soff = (int)(sc.x & 0xFFFFu), toff = (int)(sc.x >> 16);
                     int c[K], wl = 0;
-                    bool in = true;
 #pragma unroll
                     for (int j = 0; j < K; ++j) {
                         c[j] = (int)((sc.y >> (CB * j)) & CMASK);
-                        in = in && (c[j] < e[j]);
                         wl += c[j] << j;
                     }
-                    if (!in) continue;
+                    if (!full) {  // an edge tile: skip cells outside the tensor
+                        bool in = true;
+#pragma unroll
+                        for (int j = 0; j < K; ++j) in = in && (c[j] < e[j]);
+                        if (!in) continue;
+                    }
                     if (origin && s == 0) {  // H(0) = 0
                         qs[soff] = 0;
                         tbs[toff] = 0;
