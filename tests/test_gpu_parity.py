@@ -172,7 +172,7 @@ def test_dependency_wait_timeout_is_reported_not_hung():
 @pytest.mark.parametrize("kernel", [1, 2])
 def test_k3_both_fill_kernels_block_boundaries(kernel):
     """k=3 through the generic tile kernel (1) and the column kernel (2): shapes
-    straddling the column kernel's 64-row CTA blocks, 32-lane blocks and chunks."""
+    straddling the column kernel's 32-row column blocks, 32-lane blocks and 8-step blocks."""
     msa.msa_config("fill_kernel", kernel)
     try:
         shapes = [(63, 31, 40), (64, 32, 100), (65, 33, 7), (130, 70, 50), (1, 1, 200),

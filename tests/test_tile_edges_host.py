@@ -49,3 +49,10 @@ def test_tile_shape_follows_the_edge():
             assert grid == [math.ceil((n + 1) / x) for n, x in zip(lens, want)]
             sizes = msa.msa_wave_sizes(grid)
             assert len(sizes) == sum(grid) - k + 1 and sum(sizes) == math.prod(grid)  # Eq. 2, Eq. 3
+
+
+def test_planner_refuses_tensors_beyond_32_bit_tile_blocks():
+    msa.msa_config("fill_kernel", 1)
+    with pytest.raises(msa.MsaError) as ei:
+        msa.msa_tile_shape([400, 400, 400, 400])  # 2.6e10 cells: tile-major scratch offsets exceed 32 bits
+    assert ei.value.code == msa.MSA_ETOOBIG
