@@ -105,14 +105,14 @@ constexpr int kTileMajorMinK = 4;
 __host__ __device__ constexpr int tile_edge_candidate(int k, int idx) {
     return k == 2 ? (idx == 0 ? 16 : idx == 1 ? 32 : 64)
          : k == 3 ? (idx == 0 ? 8 : idx == 1 ? 12 : 16)
-         : k == 4 ? (idx == 0 ? 4 : idx == 1 ? 6 : 8)
+         : k == 4 ? (idx == 0 ? 4 : idx == 1 ? 5 : 6)
          : k == 5 ? (idx == 0 ? 3 : idx == 1 ? 4 : 5)
          : k == 6 ? (idx == 0 ? 2 : idx == 1 ? 3 : 4)
          : k == 7 ? (idx == 0 ? 2 : idx == 1 ? 3 : 0)
          : (idx == 0 ? 2 : 0);
 }
 __host__ __device__ constexpr int tile_edge_default(int k) {
-    return k == 2 ? 32 : k == 3 ? 12 : k == 4 ? 6 : k == 5 ? 4 : k == 6 ? 3 : 2;
+    return k == 2 ? 32 : k == 3 ? 12 : k == 4 ? 5 : k == 5 ? 4 : k == 6 ? 3 : 2;
 }
 __host__ __device__ constexpr bool tile_edge_valid(int k, int edge) {
     return edge > 0 && (tile_edge_candidate(k, 0) == edge || tile_edge_candidate(k, 1) == edge ||
@@ -169,7 +169,7 @@ __host__ __device__ constexpr int64_t tb_col_bytes(int rho2) { return (int64_t)(
 // staged row holds at most round_up(D + 16, 16) bytes); larger k reads cells
 // directly.
 __host__ __device__ constexpr int traceback_box(int k) { return k == 2 ? 192 : 28; }
-constexpr int kTracebackSmem = 72 * 1024;
+constexpr int kTracebackSmem = 224 * 1024;  // two 112 KB windows (column layout)
 // The traceback tensor's last axis is padded to this many bytes (16-byte rows).
 constexpr int kTbRowAlign = 16;
 

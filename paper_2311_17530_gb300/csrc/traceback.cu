@@ -1,16 +1,18 @@
 // Traceback (section 2): from the far corner follow the stored move of every
 // cell back to the origin, then score the path.
 //
-// One CTA of 256 threads per problem. The walk is a chain of dependent reads, so
-// thread 0 walks; the rest of the CTA stages the data it reads:
-//   * column layout (k = 3 column kernel): windows of one column, as many CTA
-//     times as fit in shared memory of the warp blocks and lanes the walk can
-//     still reach (cp.async by all threads), for about as many CTA times as a
-//     diagonal walk needs to leave the column; every move lowers the CTA time
-//     T = x2 + l + (x0 mod WR) by its popcount, so a window of n times holds at
-//     least n / 3 moves unless the walk leaves the column;
-//   * row-major layout, k <= 3: boxes [x - D, x] (rows of the last axis copied in
-//     16-byte granules);
+// One CTA of 256 threads per problem. The walk is a chain of dependent reads
+// kept in registers:
+//   * column layout (k = 3 column kernel): thread 0 walks alone. Per window it
+//     issues one bulk copy (cp.async.bulk, completion on an mbarrier) of whole
+//     CTA-time rows of the current column -- as many times as a diagonal walk
+//     needs to leave the column, within shared memory -- and L2 prefetches of the
+//     windows it is likely to need next (the same column further down, and the
+//     three neighbouring columns around their predicted entry times). Every move
+//     lowers the CTA time T = x2 + l + (x0 mod WR) by its popcount, so a window
+//     holds at least its length / 3 moves unless the walk leaves the column;
+//   * row-major layout, k <= 3: boxes [x - D, x] staged by the CTA (rows of the
+//     last axis copied in 16-byte granules);
 //   * k >= 4 (row-major or tile-major; short paths, large boxes): no staging; warp 0
 //     loads the traceback bytes of the current cell and of all its predecessors
 //     in one round trip, which fixes two moves.
@@ -42,12 +44,12 @@ struct WalkState {
 };
 
 // Validates a move at position x and records it; false ends the walk with a failure.
-__device__ __forceinline__ bool take_move(int K, int m, int *x, const ProblemDesc &P, const IODesc &io, int &ncols) {
-    bool bad = m == 0 || (m >> K) != 0 || ncols >= P.len_sum;
+__device__ __forceinline__ bool take_move(int K, int m, int *x, uint8_t *masks, int len_sum, int &ncols) {
+    bool bad = m == 0 || (m >> K) != 0 || ncols >= len_sum;
     for (int i = 0; i < K; ++i)
         if (((m >> i) & 1) && x[i] == 0) bad = true;
     if (bad) return false;
-    io.masks[ncols++] = (uint8_t)m;
+    masks[ncols++] = (uint8_t)m;
     for (int i = 0; i < K; ++i) x[i] -= (m >> i) & 1;
     return true;
 }
@@ -58,73 +60,203 @@ __device__ __forceinline__ bool at_origin(int K, const int *x) {
     return true;
 }
 
-// Column layout of the k = 3 column kernel.
-__device__ void walk_col3(const ProblemDesc &P, const IODesc &io, unsigned char *win, WalkState &ws) {
-    const int tid = threadIdx.x;
-    const int NB = P.G[1];
-    const int rho2 = P.rho[2];
-    const int64_t colb = c3::tb_col_bytes(rho2);
-    const int nT = c3::nsteps(rho2);
-    while (true) {
-        __syncthreads();
-        if (ws.fail || at_origin(3, ws.x)) break;
-        const int x0 = ws.x[0], x1 = ws.x[1], x2 = ws.x[2];
-        const int cA = x0 / c3::WR, cB = x1 >> 5;
-        const unsigned char *col = P.tb + (int64_t)(cA * NB + cB) * colb;
-        // window: the walk only moves to lower rows and lanes, so only warp blocks
-        // 0 .. w and lanes 0 .. l are staged (16-byte runs from the start of each
-        // warp block's 32 * R bytes), for as many CTA times as the shared memory
-        // holds (up to 255): [t_hi - nt + 1, t_hi]
-        constexpr int kRowB = 32 * c3::R;                              // bytes per (time, warp block)
-        const int nw = x0 % c3::WR / c3::R + 1;                        // warp blocks staged
-        const int ncp = ((x1 & 31) * c3::R + c3::R + 15) / 16;         // 16-byte runs per warp block
-        const int per_t = nw * ncp;                                    // runs per CTA time
-        // mostly diagonal paths leave the column after about min(row, lane) moves
-        // of three CTA times each: stage that much (plus slack), within the memory
-        const int nt = min(min(255, kTracebackSmem / (16 * per_t)), 3 * min(x0 % c3::WR, x1 & 31) + 24);
-        const int t_hi = x2 + (x1 & 31) + x0 % c3::WR;
-        const int t_lo = t_hi - nt + 1;
-        for (int i = tid; i < nt * per_t; i += kTbThreads) {
-            const int row = i / per_t, rem = i - row * per_t;
-            const int w = rem / ncp, part = rem - w * ncp;
-            const int tt = t_lo + row;
-            if (tt >= 0 && tt < nT)
-                cp_async_16(win + 16 * i, col + (int64_t)(tt + c3::U) * (c3::W * kRowB) + w * kRowB + 16 * part);
-        }
-        cp_async_wait_all();
-        __syncthreads();
-        if (tid == 0) {
-            int *x = ws.x;
-            const int before = ws.ncols;
-            while (!at_origin(3, x)) {
-                const int rho = x[0] % c3::WR, l = x[1] & 31;
-                const int tt = x[2] + l + rho;
-                if (x[0] / c3::WR != cA || (x[1] >> 5) != cB || tt < t_lo) break;
-                const int byte = l * c3::R + rho % c3::R;  // < ncp * 16: l and rho only decrease in a column
-                const int m = win[((tt - t_lo) * nw + rho / c3::R) * (16 * ncp) + byte];
-                if (!take_move(3, m, x, P, io, ws.ncols)) {
-                    ws.fail = 1;
-                    break;
-                }
-            }
-            if (ws.ncols == before && !at_origin(3, x)) ws.fail = 1;  // a window must advance the walk
-        }
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// One bulk copy global -> shared whose bytes complete the barrier's current phase.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // earlier reads of dst come first
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the completion of phase `parity`; false after about a second.
+__device__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15) == 15 && global_ns() - t0 > 1000000000ull) return false;
     }
+    return false;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *src, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ int lds_u8(unsigned addr) {
+    unsigned v;
+    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(v) : "r"(addr));
+    return (int)v;
+}
+__device__ __forceinline__ void stg_u8(uint8_t *p, int v) {
+    asm volatile("st.global.u8 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Column layout of the k = 3 column kernel: inside column (A, B) the byte of the
+// cell with CTA row rho and lane l at CTA time T is at
+// (T + U) * kRowB + (rho / R) * 32 R + l * R + rho mod R, so the rows of CTA times
+// [t_lo, t_hi] are one contiguous run. The walk only moves to lower rows, lanes
+// and times inside a column, so a window is usable from any entry point it holds.
+// Two window buffers: while thread 0 walks one, the other receives the window of
+// the column the walk is predicted to enter next (a mostly diagonal walk leaves
+// through whichever of row and lane is smaller, at a CTA time that follows from
+// the entry point); a walk that enters anything else loads its window on demand.
+struct ColWindow {
+    int a, b, t_lo, t_hi;
+};
+
+__device__ void walk_col3(const ProblemDesc &P, const IODesc &io, unsigned char *win, WalkState &ws) {
+    static_assert(c3::WR == 32 && c3::R == 4, "index arithmetic below assumes WR = 32, R = 4");
+    constexpr int kRowB = c3::W * 32 * c3::R;         // bytes of one CTA time of a column
+    constexpr int kBuf = kTracebackSmem / 2;          // one window buffer
+    constexpr int kCap = kBuf / kRowB;                // CTA times per window
+    constexpr int kAhead = 8;                         // predicted windows end this far above the entry
+    __shared__ __align__(8) uint64_t bar[2];
+    if (threadIdx.x != 0) return;
+    const int NA = P.G[0], NB = P.G[1];
+    const int nT = c3::nsteps(P.rho[2]);
+    const int64_t colb = c3::tb_col_bytes(P.rho[2]);
+    const unsigned char *tb = P.tb;
+    uint8_t *masks = io.masks;
+    const int len_sum = P.len_sum;
+    int x0 = ws.x[0], x1 = ws.x[1], x2 = ws.x[2];
+    int ncols = ws.ncols;
+    bool fail = ((uintptr_t)tb & 15) != 0;
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    unsigned phase[2] = {0, 0};
+    bool inflight[2] = {false, false};
+    ColWindow held[2] = {{-1, -1, 0, -1}, {-1, -1, 0, -1}};
+    auto load = [&](int i, ColWindow w) {  // rows [t_lo, t_hi] of column (a, b) into buffer i
+        bulk_load(win + i * kBuf, tb + (int64_t)(w.a * NB + w.b) * colb + (int64_t)(w.t_lo + c3::U) * kRowB,
+                  (unsigned)(w.t_hi - w.t_lo + 1) * kRowB, &bar[i]);
+        held[i] = w;
+        inflight[i] = true;
+    };
+    auto land = [&](int i) {  // bounded wait for buffer i's copy
+        if (!inflight[i]) return true;
+        inflight[i] = false;
+        const bool ok = mbar_wait(&bar[i], phase[i]);
+        phase[i] ^= 1;
+        if (!ok) mbar_wait(&bar[i], phase[i] ^ 1);  // let it land before the CTA may exit
+        return ok;
+    };
+    auto prefetch = [&](int a, int b, int lo, int hi) {  // L2 prefetch, clipped to the column
+        if (a < 0 || b < 0 || a >= NA || b >= NB) return;
+        lo = max(lo, 0);
+        hi = min(hi, nT - 1);
+        if (lo <= hi)
+            prefetch_l2(tb + (int64_t)(a * NB + b) * colb + (int64_t)(lo + c3::U) * kRowB,
+                        (unsigned)(hi - lo + 1) * kRowB);
+    };
+    int cur = 0;
+    while (!fail && (x0 | x1 | x2) != 0) {
+        const int A = x0 >> 5, B = x1 >> 5, rho = x0 & 31, l = x1 & 31;
+        const int T = x2 + l + rho;
+        // the window holding the entry point: the predicted one, else a demand load
+        // of as many CTA times as a diagonal walk needs to leave the column
+        const int o = 1 - cur;
+        if (held[o].a == A && held[o].b == B && T >= held[o].t_lo && T <= held[o].t_hi)
+            cur = o;  // buffer cur's copy is landed: it held the previous window
+        else
+            load(cur, {A, B, max(0, T - min(kCap, 3 * min(rho, l) + 24) + 1), T});
+        // predicted next column, and its CTA time at entry after diagonal moves
+        const int d = min(rho, l) + 1;
+        int pa = A, pb = B, pt;
+        if (rho < l) {
+            pa = A - 1;
+            pt = x2 - d + (l - d) + 31;
+        } else if (l < rho) {
+            pb = B - 1;
+            pt = x2 - d + 31 + (rho - d);
+        } else {
+            pa = A - 1;
+            pb = B - 1;
+            pt = x2 - d + 62;
+        }
+        const int nxt = 1 - cur;
+        if (!land(nxt)) {
+            fail = true;
+            break;
+        }
+        if (pa >= 0 && pb >= 0 && x2 - d >= 0) {
+            const int hi = min(pt + kAhead, nT - 1);
+            load(nxt, {pa, pb, max(0, hi - kCap + 1), hi});
+        } else {
+            held[nxt] = {-1, -1, 0, -1};
+        }
+        // the other candidates only into L2: further down this column, the other neighbours
+        prefetch(A, B, held[cur].t_lo - 48, held[cur].t_lo - 1);
+        if (!(pa == A - 1 && pb == B)) prefetch(A - 1, B, pt - 64, pt + kAhead);
+        if (!(pa == A && pb == B - 1)) prefetch(A, B - 1, pt - 64, pt + kAhead);
+        if (!land(cur)) {
+            fail = true;
+            break;
+        }
+        const int t_lo = held[cur].t_lo;
+        const unsigned wbase = smem_u32(win + cur * kBuf) - (unsigned)(t_lo * kRowB);
+        const int before = ncols;
+        while ((x0 | x1 | x2) != 0) {
+            const int r = x0 & 31, ln = x1 & 31;
+            const int tt = x2 + ln + r;
+            if ((x0 >> 5) != A || (x1 >> 5) != B || tt < t_lo) break;
+            const int m = lds_u8(wbase + (unsigned)(tt * kRowB + (r >> 2) * (32 * c3::R) + ln * c3::R + (r & 3)));
+            const int zero = (x0 == 0) | ((x1 == 0) << 1) | ((x2 == 0) << 2);
+            if ((unsigned)(m - 1) > 6u || (m & zero) != 0 || ncols >= len_sum) {
+                fail = true;
+                break;
+            }
+            stg_u8(masks + ncols, m);
+            ++ncols;
+            x0 -= m & 1;
+            x1 -= (m >> 1) & 1;
+            x2 -= m >> 2;
+        }
+        if (ncols == before) fail = true;  // a window must advance the walk
+    }
+    land(0);
+    land(1);
+    ws.x[0] = x0;
+    ws.x[1] = x1;
+    ws.x[2] = x2;
+    ws.ncols = ncols;
+    if (fail) ws.fail = 1;
 }
 
 // Row-major layout, boxes [x - D, x] (k <= 3).
+template <int K>
 __device__ void walk_boxes(const ProblemDesc &P, const IODesc &io, unsigned char *box, WalkState &ws) {
     const int tid = threadIdx.x;
-    const int K = P.k;
     const int D = traceback_box(K);
     constexpr int G = 16;
-    int64_t ts[MSA_MAX_K];
+    int64_t ts[K];
     for (int i = 0; i < K; ++i) ts[i] = P.tbstride[i];
+    const int len_sum = P.len_sum;
     while (true) {
         __syncthreads();
         if (ws.fail || at_origin(K, ws.x)) break;
-        int lo[MSA_MAX_K], ext[MSA_MAX_K];
-        int64_t bs[MSA_MAX_K];
+        int lo[K], ext[K];
+        int64_t bs[K];
         for (int i = 0; i < K; ++i) lo[i] = max(0, ws.x[i] - D);
         const int a = lo[K - 1] & ~(G - 1);
         const int rowb = round_up(ws.x[K - 1] - a + 1, G);
@@ -153,14 +285,17 @@ __device__ void walk_boxes(const ProblemDesc &P, const IODesc &io, unsigned char
         cp_async_wait_all();
         __syncthreads();
         if (tid == 0) {
-            int *x = ws.x;
-            const int before = ws.ncols;
+            int x[K];  // registers, not shared memory, on the dependent chain
+            for (int i = 0; i < K; ++i) x[i] = ws.x[i];
+            int ncols = ws.ncols;
+            const int before = ncols;
+            bool fail = false;
             int64_t li = x[K - 1] - a;
             for (int i = 0; i < K - 1; ++i) li += (int64_t)(x[i] - lo[i]) * bs[i];
             while (!at_origin(K, x)) {
                 const int m = box[li];
-                if (!take_move(K, m, x, P, io, ws.ncols)) {
-                    ws.fail = 1;
+                if (!take_move(K, m, x, io.masks, len_sum, ncols)) {
+                    fail = true;
                     break;
                 }
                 bool out = false;
@@ -171,7 +306,10 @@ __device__ void walk_boxes(const ProblemDesc &P, const IODesc &io, unsigned char
                     }
                 if (out) break;
             }
-            if (ws.ncols == before && !at_origin(K, x)) ws.fail = 1;  // a box must advance the walk
+            if (ncols == before && !at_origin(K, x)) fail = true;  // a box must advance the walk
+            for (int i = 0; i < K; ++i) ws.x[i] = x[i];
+            ws.ncols = ncols;
+            if (fail) ws.fail = 1;
         }
     }
 }
@@ -220,9 +358,9 @@ __device__ void walk_direct(const ProblemDesc &P, const IODesc &io, unsigned cha
         __syncwarp();
         if (tid == 0) {
             const int m1 = pred[0];
-            if (!take_move(K, m1, x, P, io, ncols)) {
+            if (!take_move(K, m1, x, io.masks, P.len_sum, ncols)) {
                 fail = 1;
-            } else if (!at_origin(K, x) && !take_move(K, pred[m1], x, P, io, ncols)) {
+            } else if (!at_origin(K, x) && !take_move(K, pred[m1], x, io.masks, P.len_sum, ncols)) {
                 fail = 1;
             }
         }
@@ -317,8 +455,10 @@ __global__ void __launch_bounds__(kTbThreads) traceback_kernel(const ProblemDesc
     __syncthreads();
     if (P.tb_layout == 1)
         walk_col3(P, io, smem, ws);
-    else if (K <= 3)
-        walk_boxes(P, io, smem, ws);
+    else if (K == 2)
+        walk_boxes<2>(P, io, smem, ws);
+    else if (K == 3)
+        walk_boxes<3>(P, io, smem, ws);
     else
         walk_direct(P, io, smem, ws);
     __syncthreads();
