@@ -432,9 +432,13 @@ fill_tiles_kernel(const LaunchDesc L) {
                     // (scaled pair l, h); S is stored only below 2^(K-1), the top
                     // group is consumed as it is formed, so the live state stays
                     // small enough for registers.
-                    int acc = kNeg;
+                    // NACC independent max chains (max is associative and commutative)
+                    constexpr int NACC = K <= 3 ? 1 : K <= 5 ? 2 : 4;
+                    int accs[NACC];
 #pragma unroll
-                    for (int i = 0; i < K; ++i) acc = max(acc, qs[soff - geo_sh(K, E, i)]);
+                    for (int i = 0; i < NACC; ++i) accs[i] = kNeg;
+#pragma unroll
+                    for (int i = 0; i < K; ++i) accs[i % NACC] = max(accs[i % NACC], qs[soff - geo_sh(K, E, i)]);
                     int S[1 << (K - 1)];
                     S[0] = 0;
                     S[1] = 0;  // the singleton {0}: no pair
@@ -456,9 +460,14 @@ fill_tiles_kernel(const LaunchDesc L) {
                         for (int r2 = 0; r2 < (1 << h); ++r2) {
                             const int sm = S[r2] + T[r2];
                             if (h < K - 1) S[r2 | (1 << h)] = sm;
-                            if (r2 != 0) acc = __viaddmax_s32(qs[soff - move_soff(K, E, r2 | (1 << h))], sm, acc);
+                            if (r2 != 0)
+                                accs[r2 % NACC] =
+                                    __viaddmax_s32(qs[soff - move_soff(K, E, r2 | (1 << h))], sm, accs[r2 % NACC]);
                         }
                     }
+                    int acc = accs[0];
+#pragma unroll
+                    for (int i = 1; i < NACC; ++i) acc = max(acc, accs[i]);
                     const int tmask = (Wo + wl - acc) & MASKB;
                     qs[soff] = acc + tmask;
                     tbs[toff] = (unsigned char)tmask;

@@ -214,23 +214,32 @@ __device__ void walk_col3(const ProblemDesc &P, const IODesc &io, unsigned char 
             break;
         }
         const int t_lo = held[cur].t_lo;
-        const unsigned wbase = smem_u32(win + cur * kBuf) - (unsigned)(t_lo * kRowB);
+        const unsigned wlo = smem_u32(win + cur * kBuf);
+        const unsigned wbase = wlo - (unsigned)(t_lo * kRowB);
         const int before = ncols;
-        while ((x0 | x1 | x2) != 0) {
-            const int r = x0 & 31, ln = x1 & 31;
-            const int tt = x2 + ln + r;
-            if ((x0 >> 5) != A || (x1 >> 5) != B || tt < t_lo) break;
-            const int m = lds_u8(wbase + (unsigned)(tt * kRowB + (r >> 2) * (32 * c3::R) + ln * c3::R + (r & 3)));
+        // The next cell's byte is loaded before this move's checks branch, so the
+        // branches resolve under the load's latency; a next cell outside the
+        // window reads the window's first byte instead (in bounds, unused).
+        int m = lds_u8(wbase + (unsigned)(T * kRowB + (rho >> 2) * (32 * c3::R) + l * c3::R + (rho & 3)));
+        while (true) {
             const int zero = (x0 == 0) | ((x1 == 0) << 1) | ((x2 == 0) << 2);
-            if ((unsigned)(m - 1) > 6u || (m & zero) != 0 || ncols >= len_sum) {
+            const bool bad = ((unsigned)(m - 1) > 6u) | ((m & zero) != 0) | (ncols >= len_sum);
+            const int y0 = x0 - (m & 1), y1 = x1 - ((m >> 1) & 1), y2 = x2 - (m >> 2);
+            const int r = y0 & 31, ln = y1 & 31, tt = y2 + ln + r;
+            const bool in = ((y0 >> 5) == A) & ((y1 >> 5) == B) & (tt >= t_lo) & ((y0 | y1 | y2) != 0);
+            const int mn =
+                lds_u8(in ? wbase + (unsigned)(tt * kRowB + (r >> 2) * (32 * c3::R) + ln * c3::R + (r & 3)) : wlo);
+            if (bad) {
                 fail = true;
                 break;
             }
             stg_u8(masks + ncols, m);
             ++ncols;
-            x0 -= m & 1;
-            x1 -= (m >> 1) & 1;
-            x2 -= m >> 2;
+            x0 = y0;
+            x1 = y1;
+            x2 = y2;
+            if (!in) break;
+            m = mn;
         }
         if (ncols == before) fail = true;  // a window must advance the walk
     }
@@ -290,21 +299,36 @@ __device__ void walk_boxes(const ProblemDesc &P, const IODesc &io, unsigned char
             int ncols = ws.ncols;
             const int before = ncols;
             bool fail = false;
-            int64_t li = x[K - 1] - a;
-            for (int i = 0; i < K - 1; ++i) li += (int64_t)(x[i] - lo[i]) * bs[i];
-            while (!at_origin(K, x)) {
-                const int m = box[li];
-                if (!take_move(K, m, x, io.masks, len_sum, ncols)) {
+            const unsigned bbase = smem_u32(box);
+            int li = x[K - 1] - a;
+            for (int i = 0; i < K - 1; ++i) li += (x[i] - lo[i]) * (int)bs[i];
+            // as in the column walk: the next byte is loaded before this move's
+            // checks branch; a next cell outside the box reads byte 0 (unused)
+            int m = lds_u8(bbase + li);
+            while (true) {
+                int zero = 0, y[K], lj = li;
+                bool out = false, at0 = true;
+                for (int i = 0; i < K; ++i) {
+                    const int b = (m >> i) & 1;
+                    zero |= (x[i] == 0) << i;
+                    y[i] = x[i] - b;
+                    lj -= b * (int)bs[i];
+                    out |= y[i] < lo[i];
+                    at0 &= y[i] == 0;
+                }
+                const bool bad = (m == 0) | ((m >> K) != 0) | ((m & zero) != 0) | (ncols >= len_sum);
+                const bool in = !out & !at0;
+                const int mn = lds_u8(bbase + (in ? lj : 0));
+                if (bad) {
                     fail = true;
                     break;
                 }
-                bool out = false;
-                for (int i = 0; i < K; ++i)
-                    if ((m >> i) & 1) {
-                        li -= bs[i];
-                        if (x[i] < lo[i]) out = true;
-                    }
-                if (out) break;
+                stg_u8(io.masks + ncols, m);
+                ++ncols;
+                for (int i = 0; i < K; ++i) x[i] = y[i];
+                li = lj;
+                if (!in) break;
+                m = mn;
             }
             if (ncols == before && !at_origin(K, x)) fail = true;  // a box must advance the walk
             for (int i = 0; i < K; ++i) ws.x[i] = x[i];
