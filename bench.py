@@ -132,23 +132,31 @@ def time_oracle(p, target_cells: float):
     return q, dt
 
 
-def kernel_source_digest() -> str:
+# Source files each fill kernel is compiled from (its own file and the headers it includes).
+KERNEL_SOURCES = {
+    "fill_col3": ["csrc/fill_col3.cu", "csrc/api_internal.h", "csrc/plan.h", "csrc/internal.h",
+                  "csrc/device_common.cuh", "../include/msadp.h"],
+    "fill_tiles": ["csrc/fill_tiles.cuh"] + [f"csrc/fill_tiles_k{k}.cu" for k in range(2, 9)] +
+                  ["csrc/internal.h", "csrc/device_common.cuh", "../include/msadp.h"],
+}
+
+
+def kernel_source_digest(kernel: str) -> str:
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2311_17530_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    pkg = os.path.join(ROOT, "paper_2311_17530_gb300")
+    for name in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.normpath(os.path.join(pkg, name)), "rb").read())
     return h.hexdigest()[:16]
 
 
 def measured_traffic(workload: str, kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if taken on this source."""
+    """DRAM bytes per launch from a committed ncu summary, if taken on this kernel's source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get(f"{kernel}:{workload}")
     except Exception:
         return None
-    if not rec or rec.get("source_digest") != kernel_source_digest():
+    if not rec or rec.get("source_digest") != kernel_source_digest(kernel):
         return None
     return rec.get("dram_bytes_per_launch")
 

@@ -128,6 +128,7 @@ struct ColWindow {
 __device__ void walk_col3(const ProblemDesc &P, const IODesc &io, unsigned char *win, WalkState &ws) {
     static_assert(c3::WR == 32 && c3::R == 4, "index arithmetic below assumes WR = 32, R = 4");
     constexpr int kRowB = c3::W * 32 * c3::R;         // bytes of one CTA time of a column
+    static_assert(kRowB == 1024, "the walk steps T by shifting the move count by 10");
     constexpr int kBuf = kTracebackSmem / 2;          // one window buffer
     constexpr int kCap = kBuf / kRowB;                // CTA times per window
     constexpr int kAhead = 8;                         // predicted windows end this far above the entry
@@ -218,17 +219,25 @@ __device__ void walk_col3(const ProblemDesc &P, const IODesc &io, unsigned char 
         const unsigned wbase = wlo - (unsigned)(t_lo * kRowB);
         const int before = ncols;
         // The next cell's byte is loaded before this move's checks branch, so the
-        // branches resolve under the load's latency; a next cell outside the
-        // window reads the window's first byte instead (in bounds, unused).
-        int m = lds_u8(wbase + (unsigned)(T * kRowB + (rho >> 2) * (32 * c3::R) + l * c3::R + (rho & 3)));
+        // branches resolve under the load's latency; an address below the window
+        // is clamped to its first byte (in bounds, unused: the walk leaves).
+        unsigned a = wbase + (unsigned)(T * kRowB + (rho >> 2) * (32 * c3::R) + l * c3::R + (rho & 3));
+        int m = lds_u8(a);
         while (true) {
+            // next address: every moved axis lowers T (kRowB bytes); axis 0 also
+            // lowers the row (1 byte, or 125 when it crosses a warp block of R
+            // rows), axis 1 the lane (R bytes). The part below kRowB is a byte
+            // table indexed by the mask (selected by the row's position in its block).
+            const int mm = m & 7;
+            const unsigned small = __byte_perm((x0 & 3) ? 0x05040100u : 0x81047d00u,
+                                               (x0 & 3) ? 0x05040100u : 0x81047d00u, (unsigned)mm);
+            const unsigned an = (unsigned)max((int)a - (__popc(mm) << 10) - (int)small, (int)wlo);
+            const int mn = lds_u8(an);
             const int zero = (x0 == 0) | ((x1 == 0) << 1) | ((x2 == 0) << 2);
             const bool bad = ((unsigned)(m - 1) > 6u) | ((m & zero) != 0) | (ncols >= len_sum);
             const int y0 = x0 - (m & 1), y1 = x1 - ((m >> 1) & 1), y2 = x2 - (m >> 2);
-            const int r = y0 & 31, ln = y1 & 31, tt = y2 + ln + r;
-            const bool in = ((y0 >> 5) == A) & ((y1 >> 5) == B) & (tt >= t_lo) & ((y0 | y1 | y2) != 0);
-            const int mn =
-                lds_u8(in ? wbase + (unsigned)(tt * kRowB + (r >> 2) * (32 * c3::R) + ln * c3::R + (r & 3)) : wlo);
+            const bool in = ((y0 >> 5) == A) & ((y1 >> 5) == B) & (y2 + (y1 & 31) + (y0 & 31) >= t_lo) &
+                            ((y0 | y1 | y2) != 0);
             if (bad) {
                 fail = true;
                 break;
@@ -240,6 +249,7 @@ __device__ void walk_col3(const ProblemDesc &P, const IODesc &io, unsigned char 
             x2 = y2;
             if (!in) break;
             m = mn;
+            a = an;
         }
         if (ncols == before) fail = true;  // a window must advance the walk
     }
