@@ -62,7 +62,7 @@ __host__ __device__ constexpr int tiles_cta_fixed_bytes() {
     return round_up(geo_vol(K, E) * 8, 16) + round_up(geo_planes(K, E) + 1, 4) * 4 + round_up(geo_planes(K, E), 4) * 4 +
            tiles_tm_cta_bytes<K, E>();
 }
-// Warps per CTA: the count (up to 8, 4 for k > 5) that keeps the most warps
+// Warps per CTA: the count (up to TilesCfg::kMax) that keeps the most warps
 // resident per SM within its shared memory (227 KB per CTA, 228 KB per SM,
 // 1 KB reserved per CTA), preferring fewer warps per CTA on ties.
 constexpr int kSmemPerSm = 228 * 1024, kSmemPerCta = 227 * 1024, kSmemReservedPerCta = 1024;
@@ -84,7 +84,7 @@ __host__ __device__ constexpr int tiles_best_warps(int kmax) {
 }
 template <int K, int E>
 struct TilesCfg {
-    static constexpr int kMax = 8;
+    static constexpr int kMax = K == 6 ? 16 : 8;  // warps per CTA considered (k = 6 tiles need more to fill an SM)
     static constexpr int kFit = (kSmemPerCta - tiles_cta_fixed_bytes<K, E>()) / tiles_warp_bytes<K, E>();
     static constexpr int WARPS = tiles_best_warps<K, E>(kMax);
     static_assert(kFit >= 1, "tile does not fit in shared memory");
@@ -179,6 +179,51 @@ fill_tiles_kernel(const LaunchDesc L) {
             if (live && lane == __ffs(same & act) - 1) pcur[s] += __popc(same);
             __syncwarp();
         }
+    __syncthreads();
+    // Interleave each plane's cells by the shared-memory bank of their score
+    // slot (soff mod 32, round-robin over banks: every bank's first cell, then
+    // every bank's second, ...). All predecessor reads of a round of 32 cells
+    // are one common offset from soff, so cells of distinct banks read distinct
+    // banks in every one of them. Scratch: the warp's tile area, unused until
+    // the tiles start.
+    {
+        const int nwarps = (int)(blockDim.x >> 5);
+        int *tot = reinterpret_cast<int *>(wbase + warp * tiles_warp_bytes<K, E>());
+        int *rank = tot + 32;
+        for (int p = warp; p < PLANES; p += nwarps) {
+            const int b0 = pstart[p], n = pstart[p + 1] - b0;
+            if (n <= 32 || 136 + n * 12 > tiles_warp_bytes<K, E>()) continue;
+            uint2 *tmp = reinterpret_cast<uint2 *>(rank + round_up(n, 2));
+            tot[lane] = 0;
+            __syncwarp();
+            for (int c0 = 0; c0 < n; c0 += 32) {  // rank among the plane's earlier cells of the same bank
+                const int i = c0 + lane;
+                const bool live = i < n;
+                const uint2 e = live ? sched[b0 + i] : make_uint2(0, 0);
+                const int bank = live ? (int)(e.x & 31) : -1;
+                const unsigned peers = __match_any_sync(kFull, bank);
+                const int r = live ? tot[bank] + __popc(peers & ((1u << lane) - 1)) : 0;
+                __syncwarp();
+                if (live && lane == __ffs(peers) - 1) tot[bank] += __popc(peers);
+                if (live) {
+                    tmp[i] = e;
+                    rank[i] = r;
+                }
+                __syncwarp();
+            }
+            for (int i = lane; i < n; i += 32) {  // position of (rank, bank) in round-robin order
+                const uint2 e = tmp[i];
+                const int bank = (int)(e.x & 31), r = rank[i];
+                int pos = 0;
+                for (int b2 = 0; b2 < 32; ++b2) {
+                    const int t = tot[b2];
+                    pos += min(t, r) + (b2 < bank && t > r ? 1 : 0);
+                }
+                sched[b0 + pos] = e;
+            }
+            __syncwarp();
+        }
+    }
     __syncthreads();
 
     if constexpr (TM) {
