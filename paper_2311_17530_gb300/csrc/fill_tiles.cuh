@@ -57,20 +57,34 @@ __host__ __device__ constexpr int tiles_warp_bytes() {
            (K >= kTileMajorMinK ? (1 << K) * 4 + round_up(tiles_ptab_ints<K, E>() * 4, 16) : 0);
 }
 __host__ __device__ constexpr int pair_index(int K, int l, int h) { return l * K - l * (l + 1) / 2 + (h - l - 1); }
+// Warps that fill one tile together: 2 where one warp's tile buffers leave too
+// few warps resident (k = 6, E = 3: 16 KB of halo'd scores per tile).
+template <int K, int E>
+__host__ __device__ constexpr int tiles_group() {
+    return K == 6 && E == 3 ? 2 : 1;
+}
+// plane scratch: the schedule's running plane counts, later the halo-table scan
+// (one count per warp plus the total: up to 32 warps where tiles take groups)
+template <int K, int E>
+__host__ __device__ constexpr int tiles_pcur_ints() {
+    return round_up(tiles_group<K, E>() > 1 && geo_planes(K, E) < 33 ? 33 : geo_planes(K, E), 4);
+}
 template <int K, int E>
 __host__ __device__ constexpr int tiles_cta_fixed_bytes() {
-    return round_up(geo_vol(K, E) * 8, 16) + round_up(geo_planes(K, E) + 1, 4) * 4 + round_up(geo_planes(K, E), 4) * 4 +
+    return round_up(geo_vol(K, E) * 8, 16) + round_up(geo_planes(K, E) + 1, 4) * 4 + tiles_pcur_ints<K, E>() * 4 +
            tiles_tm_cta_bytes<K, E>();
 }
-// Warps per CTA: the count (up to TilesCfg::kMax) that keeps the most warps
-// resident per SM within its shared memory (227 KB per CTA, 228 KB per SM,
-// 1 KB reserved per CTA), preferring fewer warps per CTA on ties.
+// Warps per CTA: the count (a multiple of the group, up to TilesCfg::kMax) that
+// keeps the most warps resident per SM within its shared memory (227 KB per CTA,
+// 228 KB per SM, 1 KB reserved per CTA), preferring fewer warps per CTA on ties.
+// tiles_warp_bytes is the buffer of one tile (one group).
 constexpr int kSmemPerSm = 228 * 1024, kSmemPerCta = 227 * 1024, kSmemReservedPerCta = 1024;
 template <int K, int E>
 __host__ __device__ constexpr int tiles_best_warps(int kmax) {
-    int best = 1, best_res = 0;
-    for (int w = 1; w <= kmax; ++w) {
-        const int bytes = tiles_cta_fixed_bytes<K, E>() + w * tiles_warp_bytes<K, E>();
+    constexpr int G = tiles_group<K, E>();
+    int best = G, best_res = 0;
+    for (int w = G; w <= kmax; w += G) {
+        const int bytes = tiles_cta_fixed_bytes<K, E>() + (w / G) * tiles_warp_bytes<K, E>();
         if (bytes > kSmemPerCta) break;
         int ctas = kSmemPerSm / (bytes + kSmemReservedPerCta);
         if (ctas > 32) ctas = 32;
@@ -84,12 +98,13 @@ __host__ __device__ constexpr int tiles_best_warps(int kmax) {
 }
 template <int K, int E>
 struct TilesCfg {
-    static constexpr int kMax = K == 6 ? 16 : 8;  // warps per CTA considered (k = 6 tiles need more to fill an SM)
+    static constexpr int kMax = K == 6 ? 24 : 8;  // warps per CTA considered (k = 6 tiles need more to fill an SM)
     static constexpr int kFit = (kSmemPerCta - tiles_cta_fixed_bytes<K, E>()) / tiles_warp_bytes<K, E>();
     static constexpr int WARPS = tiles_best_warps<K, E>(kMax);
     static_assert(kFit >= 1, "tile does not fit in shared memory");
-    static_assert(K < kTileMajorMinK || round_up(geo_planes(K, E), 4) >= WARPS + 1,
-                  "plane scratch holds the halo-table scan");
+    static_assert(WARPS % tiles_group<K, E>() == 0 && WARPS / tiles_group<K, E>() <= 15,
+                  "whole groups, one named barrier each");
+    static_assert(K < kTileMajorMinK || tiles_pcur_ints<K, E>() >= WARPS + 1, "plane scratch holds the halo-table scan");
     static_assert(geo_volh(K, E) < 65536 && geo_vol(K, E) < 65536, "schedule entries hold 16-bit offsets");
     static_assert(E < (K <= 4 ? 256 : 16) && tile_ext(K, E, K - 1) < (K <= 4 ? 256 : 16),
                   "packed local coordinates");
@@ -97,7 +112,31 @@ struct TilesCfg {
 
 template <int K, int E>
 __host__ __device__ constexpr int tiles_smem_bytes() {
-    return tiles_cta_fixed_bytes<K, E>() + TilesCfg<K, E>::WARPS * tiles_warp_bytes<K, E>();
+    return tiles_cta_fixed_bytes<K, E>() + TilesCfg<K, E>::WARPS / tiles_group<K, E>() * tiles_warp_bytes<K, E>();
+}
+
+// Barrier and vote of the G warps that fill one tile (named barrier 1 + group).
+template <int G>
+__device__ __forceinline__ void group_sync(int grp) {
+    if constexpr (G == 1)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(32 * G) : "memory");
+}
+template <int G>
+__device__ __forceinline__ bool group_all(int grp, bool p) {
+    if constexpr (G == 1) {
+        return __all_sync(kFull, p);
+    } else {
+        unsigned r;
+        asm volatile(
+            "{\n\t.reg .pred q, rq;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred rq, %2, %3, q;\n\tselp.u32 %0, 1, 0, "
+            "rq;\n\t}"
+            : "=r"(r)
+            : "r"((unsigned)p), "r"(1 + grp), "r"(32 * G)
+            : "memory");
+        return r != 0;
+    }
 }
 
 template <int K, int E>
@@ -120,13 +159,15 @@ fill_tiles_kernel(const LaunchDesc L) {
     int *pcur = pstart + round_up(PLANES + 1, 4);
     constexpr bool HPK = tiles_halo_packed<K, E>();  // 4-byte halo entries
     constexpr int SB = bits_for(VOLH), LB = bits_for(VOL);
-    uint2 *htab = reinterpret_cast<uint2 *>(pcur + round_up(PLANES, 4));
+    uint2 *htab = reinterpret_cast<uint2 *>(pcur + tiles_pcur_ints<K, E>());
     uint32_t *htab4 = reinterpret_cast<uint32_t *>(htab);
     uint16_t *wtab = reinterpret_cast<uint16_t *>(reinterpret_cast<unsigned char *>(htab) +
                                                   (TM ? round_up(NH * (HPK ? 4 : 8), 16) : 0));
     unsigned char *wbase = reinterpret_cast<unsigned char *>(htab) + tiles_tm_cta_bytes<K, E>();
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int G = tiles_group<K, E>(), TG = 32 * G;  // warps and threads per tile
+    const int grp = warp / G, gl = tid - grp * TG;        // tile group, thread in the group
 
     // Intra-tile schedule: every cell of a full tile, grouped by local index sum.
     for (int s = tid; s < PLANES; s += blockDim.x) pcur[s] = 0;
@@ -188,11 +229,12 @@ fill_tiles_kernel(const LaunchDesc L) {
     // the tiles start.
     {
         const int nwarps = (int)(blockDim.x >> 5);
-        int *tot = reinterpret_cast<int *>(wbase + warp * tiles_warp_bytes<K, E>());
+        constexpr int kScratch = tiles_warp_bytes<K, E>() / G / 16 * 16;  // per warp
+        int *tot = reinterpret_cast<int *>(wbase + grp * tiles_warp_bytes<K, E>() + (warp - grp * G) * kScratch);
         int *rank = tot + 32;
         for (int p = warp; p < PLANES; p += nwarps) {
             const int b0 = pstart[p], n = pstart[p + 1] - b0;
-            if (n <= 32 || 136 + n * 12 > tiles_warp_bytes<K, E>()) continue;
+            if (n <= 32 || 136 + n * 12 > kScratch) continue;
             uint2 *tmp = reinterpret_cast<uint2 *>(rank + round_up(n, 2));
             tot[lane] = 0;
             __syncwarp();
@@ -279,18 +321,30 @@ fill_tiles_kernel(const LaunchDesc L) {
         }
     }
 
-    int32_t *qs = reinterpret_cast<int32_t *>(wbase + warp * tiles_warp_bytes<K, E>());
+    int32_t *qs = reinterpret_cast<int32_t *>(wbase + grp * tiles_warp_bytes<K, E>());
     unsigned char *tbs = reinterpret_cast<unsigned char *>(qs) + round_up(VOLH * 4, 16);
     unsigned char *tcs = tbs + round_up(VOL, 16);
     int *nbase = reinterpret_cast<int *>(tcs + round_up(geo_codes(K, E), 16));
     int *ptab = nbase + (TM ? (1 << K) : 0);
 
+    __shared__ int2 gtick[G > 1 ? 16 : 1];  // per group: ticket, launch error seen
     while (true) {
         int t = 0;
-        if (lane == 0) t = atomicAdd(L.ticket, 1);
-        t = __shfl_sync(kFull, t, 0);
-        if ((int64_t)t >= L.ntickets) break;
-        if (ld_volatile(L.err) != 0) break;
+        if constexpr (G == 1) {
+            if (lane == 0) t = atomicAdd(L.ticket, 1);
+            t = __shfl_sync(kFull, t, 0);
+            if ((int64_t)t >= L.ntickets) break;
+            if (ld_volatile(L.err) != 0) break;
+        } else {
+            // one thread takes the ticket and reads the launch error for the group,
+            // so that every decision below is the same in all of its warps
+            if (gl == 0) gtick[grp] = make_int2(atomicAdd(L.ticket, 1), ld_volatile(L.err));
+            group_sync<G>(grp);
+            const int2 te = gtick[grp];
+            t = te.x;
+            if ((int64_t)t >= L.ntickets) break;
+            if (te.y != 0) break;
+        }
         const uint64_t ent = L.order[t];
         const ProblemDesc &P = L.probs[(int)(ent >> 32)];
         const int64_t lin = (int64_t)(uint32_t)ent;
@@ -317,19 +371,24 @@ fill_tiles_kernel(const LaunchDesc L) {
         }
         const int64_t tile_base = P.tile_base;
 
-        // Wait for the face predecessors (one lane per axis).
+        // Wait for the face predecessors (one thread per axis).
         bool ok = true;
 #pragma unroll
         for (int j = 0; j < K; ++j)
-            if (lane == j && tco[j] > 0)
+            if (gl == j && tco[j] > 0)
                 ok = wait_at_least(&L.done[tile_base + lin - P.gstride[j]], 1, L.err, L.spin_ns);
-        if (!__all_sync(kFull, ok)) {
-            if (lane == 0) atomicCAS(L.err, 0, MSA_ETIMEOUT);
+        if (!group_all<G>(grp, ok)) {
+            if (gl == 0) atomicCAS(L.err, 0, MSA_ETIMEOUT);
             break;
         }
         __threadfence();
 
-        if (ld_volatile(&P.istat->status) == 0) {
+        bool live;
+        if constexpr (G == 1)
+            live = ld_volatile(&P.istat->status) == 0;
+        else
+            live = group_all<G>(grp, ld_volatile(&P.istat->status) == 0);
+        if (live) {
             const int A = P.A;
             const int32_t *__restrict__ tab = P.tab;
             const uint8_t *__restrict__ codes = P.codes;
@@ -339,7 +398,7 @@ fill_tiles_kernel(const LaunchDesc L) {
             // residue x_j - 1 of sequence j).
 #pragma unroll
             for (int j = 0; j < K; ++j)
-                for (int c = lane; c < tile_ext(K, E, j); c += 32) {
+                for (int c = gl; c < tile_ext(K, E, j); c += TG) {
                     const int x = o[j] + c;
                     tcs[geo_code_base(K, E, j) + c] =
                         (x >= 1 && x <= len[j]) ? codes[cofs[j] + x - 1] : (uint8_t)0;
@@ -347,8 +406,8 @@ fill_tiles_kernel(const LaunchDesc L) {
 
             if constexpr (TM) {
                 // this tile's pair tables: ptab[pair(l,h)][a*E + b] = tab[code_l(a)][code_h(b)]
-                __syncwarp();
-                for (int idx = lane; idx < tiles_ptab_ints<K, E>(); idx += 32) {
+                group_sync<G>(grp);
+                for (int idx = gl; idx < tiles_ptab_ints<K, E>(); idx += TG) {
                     const int pr = idx / (E * E), ab = idx - pr * (E * E);
                     int l = 0, rest = pr;
                     while (rest >= K - 1 - l) {
@@ -365,10 +424,10 @@ fill_tiles_kernel(const LaunchDesc L) {
             // (other SMs wrote these cells) and are issued in batches of HB before
             // their shared-memory stores, so the halo costs about one L2 round trip
             // per batch rather than one per element.
-            constexpr int HB = 8;
+            constexpr int HB = (K >= 6 ? 32 : K == 5 ? 16 : K == 4 ? 12 : 8) / G;  // measured per k
             if constexpr (TM) {
                 // lower neighbour tiles' blocks (none across the origin faces)
-                for (int S = lane + 1; S < (1 << K); S += 32) {
+                for (int S = gl + 1; S < (1 << K); S += TG) {
                     int64_t nb = lin;
                     bool ok = true;
 #pragma unroll
@@ -379,12 +438,12 @@ fill_tiles_kernel(const LaunchDesc L) {
                         }
                     nbase[S] = ok ? (int)(nb * VOL) : -1;
                 }
-                __syncwarp();
-                for (int i0 = 0; i0 < NH; i0 += 32 * HB) {
+                group_sync<G>(grp);
+                for (int i0 = 0; i0 < NH; i0 += TG * HB) {
                     int val[HB], dst[HB];
 #pragma unroll
                     for (int u = 0; u < HB; ++u) {
-                        const int i = i0 + 32 * u + lane;
+                        const int i = i0 + TG * u + gl;
                         dst[u] = -1;
                         val[u] = kNeg;
                         if (i < NH) {
@@ -412,11 +471,11 @@ fill_tiles_kernel(const LaunchDesc L) {
             }
 #pragma unroll
             for (int f = 0; f < (TM ? 0 : K); ++f) {
-                for (int i0 = 0; i0 < face_size(K, E, f); i0 += 32 * HB) {
+                for (int i0 = 0; i0 < face_size(K, E, f); i0 += TG * HB) {
                     int val[HB], dst[HB];
 #pragma unroll
                     for (int u = 0; u < HB; ++u) {
-                        const int i = i0 + 32 * u + lane;
+                        const int i = i0 + TG * u + gl;
                         int r = i, soff = 0;
                         bool in = i < face_size(K, E, f), neg = false;
                         int64_t g = 0;
@@ -439,7 +498,7 @@ fill_tiles_kernel(const LaunchDesc L) {
                         if (dst[u] >= 0) qs[dst[u]] = val[u];
                 }
             }
-            __syncwarp();
+            group_sync<G>(grp);
 
             int Wo = 0;
 #pragma unroll
@@ -447,7 +506,7 @@ fill_tiles_kernel(const LaunchDesc L) {
 
             for (int s = 0; s < PLANES; ++s) {
                 const int b = pstart[s], en = pstart[s + 1];
-                for (int idx = b + lane; idx < en; idx += 32) {
+                for (int idx = b + gl; idx < en; idx += TG) {
                     const uint2 sc = sched[idx];
                     const int soff = (int)(sc.x & 0xFFFFu), toff = (int)(sc.x >> 16);
                     int c[K], wl = 0;
@@ -517,7 +576,7 @@ fill_tiles_kernel(const LaunchDesc L) {
                     qs[soff] = acc + tmask;
                     tbs[toff] = (unsigned char)tmask;
                 }
-                __syncwarp();
+                group_sync<G>(grp);
             }
 
             // Write back scores (for successor halos) and traceback bytes.
@@ -527,12 +586,12 @@ fill_tiles_kernel(const LaunchDesc L) {
                 // this tile's blocks, contiguous (cells outside the tensor included)
                 int32_t *qb = Qw + lin * VOL;
                 uint8_t *tbb = tbw + lin * VOL;
-                for (int i = lane; i < VOL; i += 32) {
+                for (int i = gl; i < VOL; i += TG) {
                     qb[i] = qs[wtab[i]];
                     tbb[i] = tbs[i];
                 }
             }
-            for (int i = lane; i < (TM ? 0 : VOL); i += 32) {
+            for (int i = gl; i < (TM ? 0 : VOL); i += TG) {
                 int r = i, soff = 0;
                 bool in = true;
                 int64_t gq = 0, gt = 0;
@@ -550,15 +609,15 @@ fill_tiles_kernel(const LaunchDesc L) {
                     tbw[gt] = tbs[i];
                 }
             }
-            if (corner && lane == 0) {
+            if (corner && gl == 0) {
                 int soff = 0;
 #pragma unroll
                 for (int j = 0; j < K; ++j) soff += e[j] * geo_sh(K, E, j);
                 *P.qcorner = qs[soff];
             }
         }
-        __syncwarp();
-        if (lane == 0 && (int64_t)t != L.withhold) {
+        group_sync<G>(grp);
+        if (gl == 0 && (int64_t)t != L.withhold) {
             __threadfence();
             st_release(&L.done[tile_base + lin], 1);
         }
