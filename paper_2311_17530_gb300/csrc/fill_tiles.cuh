@@ -58,10 +58,11 @@ __host__ __device__ constexpr int tiles_warp_bytes() {
 }
 __host__ __device__ constexpr int pair_index(int K, int l, int h) { return l * K - l * (l + 1) / 2 + (h - l - 1); }
 // Warps that fill one tile together: 2 where one warp's tile buffers leave too
-// few warps resident (k = 6, E = 3: 16 KB of halo'd scores per tile).
+// few warps resident (k = 6, E = 3: 16 KB of halo'd scores per tile; k = 4,
+// E = 6 and k = 5, E = 4: 10-13 KB). Measured faster for these three.
 template <int K, int E>
 __host__ __device__ constexpr int tiles_group() {
-    return K == 6 && E == 3 ? 2 : 1;
+    return (K == 6 && E == 3) || (K == 4 && E == 6) || (K == 5 && E == 4) ? 2 : 1;
 }
 // plane scratch: the schedule's running plane counts, later the halo-table scan
 // (one count per warp plus the total: up to 32 warps where tiles take groups)
@@ -98,11 +99,12 @@ __host__ __device__ constexpr int tiles_best_warps(int kmax) {
 }
 template <int K, int E>
 struct TilesCfg {
-    static constexpr int kMax = K == 6 ? 24 : 8;  // warps per CTA considered (k = 6 tiles need more to fill an SM)
+    // warps per CTA considered (k = 6 and tile groups need more to fill an SM)
+    static constexpr int kMax = K == 6 || tiles_group<K, E>() > 1 ? 24 : 8;
     static constexpr int kFit = (kSmemPerCta - tiles_cta_fixed_bytes<K, E>()) / tiles_warp_bytes<K, E>();
     static constexpr int WARPS = tiles_best_warps<K, E>(kMax);
     static_assert(kFit >= 1, "tile does not fit in shared memory");
-    static_assert(WARPS % tiles_group<K, E>() == 0 && WARPS / tiles_group<K, E>() <= 15,
+    static_assert(WARPS % tiles_group<K, E>() == 0 && (tiles_group<K, E>() == 1 || WARPS / tiles_group<K, E>() <= 15),
                   "whole groups, one named barrier each");
     static_assert(K < kTileMajorMinK || tiles_pcur_ints<K, E>() >= WARPS + 1, "plane scratch holds the halo-table scan");
     static_assert(geo_volh(K, E) < 65536 && geo_vol(K, E) < 65536, "schedule entries hold 16-bit offsets");

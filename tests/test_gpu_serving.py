@@ -138,3 +138,20 @@ def test_concurrent_submitters():
     for p, res in zip(probs, results):
         want = oracle.align(p.seqs, p.alphabet, p.subst, p.gap)
         assert res == (want.score, want.rows), p.name
+
+
+def test_served_large_k_batches_equal_oracle():
+    # k = 5 and 6 requests of uneven shapes in one stream: the default tile edges for
+    # these k fill each tile with two warps, batched with other problems of the group
+    probs = []
+    for i in range(8):
+        rng = np.random.default_rng(1500 + i)
+        k = 5 if i % 2 else 6
+        hi = {5: 10, 6: 7}[k]
+        lens = [int(x) for x in rng.integers(1, hi + 1, size=k)]
+        probs.append(inputs.random_problem(1500 + i, k, lens, alphabet=inputs.DNA if i % 3 else inputs.PROTEIN,
+                                           related=bool(i % 2)))
+    got = serve(probs)
+    for p, res in zip(probs, got):
+        want = oracle.align(p.seqs, p.alphabet, p.subst, p.gap)
+        assert res == (want.score, want.rows), p.name
