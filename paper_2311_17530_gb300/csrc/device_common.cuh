@@ -49,9 +49,33 @@ __device__ __forceinline__ bool wait_at_least(const int32_t *flag, int need, con
 }
 
 // Geometry of the generic tile kernel (compile-time per k and tile edge E).
-__host__ __device__ constexpr int geo_sh(int K, int E, int i) {  // halo'd tile stride
+//
+// The halo'd score tile in shared memory is laid out with strides
+// sh_{K-1} = 1, sh_j = sh_{j+1} (ext_{j+1} + 1) + pad_j: a predecessor is still a
+// constant offset away, and the pads (found by counting, for each shape, the
+// shared-memory wavefronts of the predecessor reads of every round of 32 cells)
+// spread the cells of a plane over more of the 32 banks than power-of-two
+// strides do. Positions inside the pads are never read or written.
+__host__ __device__ constexpr int geo_pad(int K, int E, int j) {
+    constexpr int none = 0;
+    return K == 4 && E == 5   ? (j == 1 ? 1 : none)
+         : K == 4 && E == 6   ? (j == 0 ? 3 : j == 1 ? 1 : j == 2 ? 1 : none)
+         : K == 5 && E == 3   ? (j == 1 ? 3 : none)
+         : K == 5 && E == 4   ? (j == 0 ? 1 : j == 1 ? 1 : j == 2 ? 3 : none)
+         : K == 6 && E == 2   ? (j == 1 ? 1 : j == 2 ? 1 : none)
+         : K == 6 && E == 3   ? (j == 1 ? 3 : none)
+         : K == 3 && E == 12  ? (j == 0 ? 1 : j == 1 ? 1 : none)
+                              : none;
+}
+// halo'd tile stride of axis i; i = -1 gives the tile's size sh_0 (ext_0 + 1)
+__host__ __device__ constexpr int geo_sh(int K, int E, int i) {
     int s = 1;
-    for (int j = K - 1; j > i; --j) s *= tile_ext(K, E, j) + 1;
+    for (int j = K - 2; j >= i; --j) s = s * (tile_ext(K, E, j + 1) + 1) + (j >= 0 ? geo_pad(K, E, j) : 0);
+    return s;
+}
+__host__ __device__ constexpr int geo_cellsh(int K, int E) {  // cells of the halo'd tile
+    int s = 1;
+    for (int j = 0; j < K; ++j) s *= tile_ext(K, E, j) + 1;
     return s;
 }
 __host__ __device__ constexpr int geo_st(int K, int E, int i) {  // interior tile stride

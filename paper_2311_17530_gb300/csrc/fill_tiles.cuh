@@ -41,7 +41,7 @@ __host__ __device__ constexpr bool tiles_halo_packed() {
 }
 template <int K, int E>
 __host__ __device__ constexpr int tiles_tm_cta_bytes() {
-    return K >= kTileMajorMinK ? round_up((geo_volh(K, E) - geo_vol(K, E)) * (tiles_halo_packed<K, E>() ? 4 : 8), 16) +
+    return K >= kTileMajorMinK ? round_up((geo_cellsh(K, E) - geo_vol(K, E)) * (tiles_halo_packed<K, E>() ? 4 : 8), 16) +
                                      round_up(geo_vol(K, E) * 2, 16)
                                : 0;
 }
@@ -153,7 +153,7 @@ fill_tiles_kernel(const LaunchDesc L) {
     constexpr int MASKB = (1 << K) - 1;  // tie bits B = k
 
     constexpr bool TM = K >= kTileMajorMinK;  // tile-major scratch and traceback
-    constexpr int NH = VOLH - VOL;            // halo cells
+    constexpr int NH = geo_cellsh(K, E) - VOL;  // halo cells
 
     extern __shared__ __align__(16) unsigned char smem[];
     uint2 *sched = reinterpret_cast<uint2 *>(smem);
@@ -295,15 +295,17 @@ fill_tiles_kernel(const LaunchDesc L) {
             uint32_t S = 0, loff = 0;
             if (i < VOLH) {
                 int rem = i;
+                bool pad = false;
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
-                    const int d = rem / geo_sh(K, E, j);  // halo'd coordinate 0 .. E_j
+                    const int d = rem / geo_sh(K, E, j);  // halo'd coordinate 0 .. E_j (above: a pad position)
                     rem -= d * geo_sh(K, E, j);
+                    pad = pad || d > tile_ext(K, E, j);
                     const int cl = d == 0 ? tile_ext(K, E, j) - 1 : d - 1;
                     if (d == 0) S |= 1u << j;
                     loff += (uint32_t)(cl * geo_st(K, E, j));
                 }
-                halo = S != 0;
+                halo = S != 0 && !pad;
             }
             const unsigned bal = __ballot_sync(kFull, halo);
             if (lane == 0) pcur[warp] = __popc(bal);
