@@ -59,7 +59,7 @@ __device__ __forceinline__ bool wait_at_least(const int32_t *flag, int need, con
 __host__ __device__ constexpr int geo_pad(int K, int E, int j) {
     constexpr int none = 0;
     return K == 4 && E == 5   ? (j == 1 ? 1 : none)
-         : K == 4 && E == 6   ? (j == 0 ? 3 : j == 1 ? 1 : j == 2 ? 1 : none)
+         : K == 4 && E == 6   ? (j == 0 ? 5 : j == 1 ? 5 : none)
          : K == 5 && E == 3   ? (j == 1 ? 3 : none)
          : K == 5 && E == 4   ? (j == 0 ? 1 : j == 1 ? 1 : j == 2 ? 3 : none)
          : K == 6 && E == 2   ? (j == 1 ? 1 : j == 2 ? 1 : none)

@@ -112,7 +112,7 @@ __host__ __device__ constexpr int tile_edge_candidate(int k, int idx) {
          : (idx == 0 ? 2 : 0);
 }
 __host__ __device__ constexpr int tile_edge_default(int k) {
-    return k == 2 ? 32 : k == 3 ? 12 : k == 4 ? 5 : k == 5 ? 4 : k == 6 ? 3 : 2;
+    return k == 2 ? 32 : k == 3 ? 12 : k == 4 ? 6 : k == 5 ? 4 : k == 6 ? 3 : 2;
 }
 __host__ __device__ constexpr bool tile_edge_valid(int k, int edge) {
     return edge > 0 && (tile_edge_candidate(k, 0) == edge || tile_edge_candidate(k, 1) == edge ||

@@ -8,7 +8,7 @@ import pytest
 import paper_2311_17530_gb300 as msa
 
 CANDIDATES = {2: [16, 32, 64], 3: [8, 12, 16], 4: [4, 5, 6], 5: [3, 4, 5], 6: [2, 3, 4], 7: [2, 3], 8: [2]}
-DEFAULT = {2: 32, 3: 12, 4: 5, 5: 4, 6: 3, 7: 2, 8: 2}
+DEFAULT = {2: 32, 3: 12, 4: 6, 5: 4, 6: 3, 7: 2, 8: 2}
 
 
 @pytest.fixture(autouse=True)
