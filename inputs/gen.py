@@ -67,8 +67,8 @@ def dna_table(match: int = 5, mismatch: int = -4) -> np.ndarray:
     return t
 
 
-# The scoring the paper reports its similarity scores with (section 5.2): +1 for
-# a match, 0 for a mismatch, -1 for a residue against a gap (gap/gap pairs 0).
+# The scoring behind the similarity scores of section 5.2: identical residues
+# score +1, different residues 0, a residue facing a gap -1, two gaps 0.
 PAPER_GAP = -1
 
 

@@ -11,14 +11,14 @@
  *   - the k-dimensional scoring tensor has rho_i = len_i + 1 cells per axis
  *     (the initial gap character, section 3.2), N = prod rho_i cells (section 2);
  *   - every cell x != 0 is the max over its 2^k-1 lower neighbours x - e_m
- *     (section 2: "2^k-1 neighbours", generalising Eq. 1), m a non-empty subset
- *     of the sequences, bit i of m meaning "sequence i consumes its residue
- *     x_i - 1 in this column" and a clear bit meaning a gap in row i;
+ *     (section 2 counts 2^k-1 of them per cell, generalising Eq. 1), m a
+ *     non-empty subset of the sequences, bit i of m meaning that sequence i
+ *     consumes its residue x_i - 1 in this column and a clear bit a gap in row i;
  *   - the score of a move is the sum of pairs over the column (section 5.2):
  *     sub(a, b) for two residues, the gap value for a residue against a gap,
  *     0 for two gaps; pair scores are evaluated directly, O(k^2) per move
- *     (section 4, "pair-wise scores for each pair of residues");
- *   - H(0) = 0 (section 4, "if initial cell, initialize it");
+ *     (section 4 scores every pair of residues of a column);
+ *   - H(0) = 0 (section 4 initialises the origin cell);
  *   - ties go to the lowest move mask: a candidate replaces the best only when
  *     strictly greater while masks are visited in increasing order;
  *   - traceback starts at the far corner (global alignment) and follows the

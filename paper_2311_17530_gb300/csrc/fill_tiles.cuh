@@ -3,17 +3,18 @@
 // The k-dimensional tensor (section 2) is cut into hyper-tiles of compile-time
 // extents E_i (the paper's partitions of size S, section 3, but without overlap:
 // a tile reads a one-cell halo from its lower neighbours instead). Tiles are
-// handed out by an atomic ticket in wave order (tiles of equal index sum,
-// section 3: "partitions at equal distance from the origin"); a tile starts once
+// handed out by an atomic ticket in wave order (tiles of equal index sum: the
+// partitions section 3 groups by their distance from the origin); a tile starts once
 // its k face predecessors have published completion (bounded acquire waits),
 // which also covers every edge and corner predecessor transitively.
 //
-// One warp fills one tile in shared memory: the halo comes from the score
-// scratch in global memory (L2, bypassing L1), then the warp sweeps the tile's
-// own intra-tile hyperplanes (cells of equal local index sum are independent),
-// one cell per lane, each cell taking the max over its 2^k - 1 predecessors with
-// the packed-key add-max (DPX viaddmax). Finally the tile's scores and traceback
-// bytes are written back and the tile's flag is released.
+// One warp (two for a few large shapes, see tiles_group) fills one tile in
+// shared memory: the halo comes from the score scratch in global memory (L2,
+// bypassing L1), then the warp sweeps the tile's own intra-tile hyperplanes
+// (cells of equal local index sum are independent), one cell per thread, each
+// cell taking the max over its 2^k - 1 predecessors with the packed-key add-max
+// (DPX viaddmax). Finally the tile's scores and traceback bytes are written back
+// and the tile's flag is released.
 #pragma once
 
 #include "device_common.cuh"
