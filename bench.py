@@ -142,10 +142,16 @@ KERNEL_SOURCES = {
 
 
 def kernel_source_digest(kernel: str) -> str:
+    """Digest of the code (comments and blank lines removed) a fill kernel is built from."""
+    import re
     h = hashlib.sha256()
     pkg = os.path.join(ROOT, "paper_2311_17530_gb300")
     for name in KERNEL_SOURCES[kernel]:
-        h.update(open(os.path.normpath(os.path.join(pkg, name)), "rb").read())
+        src = open(os.path.normpath(os.path.join(pkg, name)), encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        code = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

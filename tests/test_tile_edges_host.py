@@ -2,11 +2,15 @@
 and the tile shape the planner reports for a chosen edge (section 3.2's
 partition size S; Eq. 2 and 3 count the waves and tiles of the resulting grid)."""
 import math
+import os
+import subprocess
 
 import pytest
 
 import paper_2311_17530_gb300 as msa
 
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2311_17530_gb300", "csrc")
 CANDIDATES = {2: [16, 32, 64], 3: [8, 12, 16], 4: [4, 5, 6], 5: [3, 4, 5], 6: [2, 3, 4], 7: [2, 3], 8: [2]}
 DEFAULT = {2: 32, 3: 12, 4: 6, 5: 4, 6: 3, 7: 2, 8: 2}
 
@@ -56,3 +60,23 @@ def test_planner_refuses_tensors_beyond_32_bit_tile_blocks():
     with pytest.raises(msa.MsaError) as ei:
         msa.msa_tile_shape([400, 400, 400, 400])  # 2.6e10 cells: tile-major scratch offsets exceed 32 bits
     assert ei.value.code == msa.MSA_ETOOBIG
+
+
+def _nvcc():
+    import shutil
+    for c in ("/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
+        if c and os.path.exists(c):
+            return c
+    return None
+
+
+@pytest.mark.skipif(_nvcc() is None, reason="needs nvcc")
+def test_padded_tile_layout_is_a_bijection(tmp_path):
+    # every compiled tile shape: halo'd cells at distinct offsets inside the
+    # buffer, predecessor offsets = sums of strides, halo-cell count (host program)
+    exe = tmp_path / "tile_geometry_check"
+    subprocess.check_call([_nvcc(), "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-I", CSRC, "-I",
+                           os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "tile_geometry_check.cu"),
+                           "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout
