@@ -3,14 +3,15 @@
 //
 // One CTA of 256 threads per problem. The walk is a chain of dependent reads
 // kept in registers:
-//   * column layout (k = 3 column kernel): thread 0 walks alone. Per window it
-//     issues one bulk copy (cp.async.bulk, completion on an mbarrier) of whole
-//     CTA-time rows of the current column -- as many times as a diagonal walk
-//     needs to leave the column, within shared memory -- and L2 prefetches of the
-//     windows it is likely to need next (the same column further down, and the
-//     three neighbouring columns around their predicted entry times). Every move
-//     lowers the CTA time T = x2 + l + (x0 mod WR) by its popcount, so a window
-//     holds at least its length / 3 moves unless the walk leaves the column;
+//   * column layout (k = 3 column kernel): thread 0 walks alone. A window is one
+//     bulk copy (cp.async.bulk, completion on an mbarrier) of whole CTA-time
+//     rows of a column -- as many times as a diagonal walk needs to leave the
+//     column, within a 112 KB buffer. While it walks one buffer, the other
+//     receives the window of the column the walk is predicted to enter next,
+//     and the other likely windows (the same column further down, the other
+//     neighbouring columns) are prefetched into L2. Every move lowers the CTA
+//     time T = x2 + l + (x0 mod WR) by its popcount, so a window holds at least
+//     its length / 3 moves unless the walk leaves the column;
 //   * row-major layout, k <= 3: boxes [x - D, x] staged by the CTA (rows of the
 //     last axis copied in 16-byte granules);
 //   * k >= 4 (row-major or tile-major; short paths, large boxes): no staging; warp 0
