@@ -429,7 +429,7 @@ fill_tiles_kernel(const LaunchDesc L) {
             // (other SMs wrote these cells) and are issued in batches of HB before
             // their shared-memory stores, so the halo costs about one L2 round trip
             // per batch rather than one per element.
-            constexpr int HB = (K >= 6 ? 32 : K == 5 ? 16 : K == 4 ? 12 : 8) / G;  // measured per k
+            constexpr int HB = (K >= 6 ? 48 : K == 5 ? (G > 1 ? 24 : 16) : K == 4 ? 16 : 8) / G;  // measured per shape
             if constexpr (TM) {
                 // lower neighbour tiles' blocks (none across the origin faces)
                 for (int S = gl + 1; S < (1 << K); S += TG) {

@@ -411,6 +411,123 @@ __device__ void walk_direct(const ProblemDesc &P, const IODesc &io, unsigned cha
     }
 }
 
+// Tile-major layout (k >= 4): the CTA stages the blocks of the tiles
+// [q - span + 1, q] per axis around the current cell's tile q (span 4, 3 or 2:
+// the largest whose blocks fit the window memory), one 16-byte-aligned copy of
+// each block, and thread 0 walks them in registers -- local coordinates, the
+// offset inside the tile and the tile's slot updated per move -- until the walk
+// leaves the staged tiles (at least (span - 1) E moves along every axis).
+template <int K>
+__device__ void walk_tiles(const ProblemDesc &P, const IODesc &io, unsigned char *smem, WalkState &ws) {
+    const int tid = threadIdx.x;
+    int E[K], lst[K];
+    int vol = 1;
+    for (int i = K - 1; i >= 0; --i) {
+        E[i] = P.E[i];
+        lst[i] = vol;
+        vol *= E[i];
+    }
+    const int slot = round_up(vol + 15, 16);  // a block copied from the 16-byte boundary below it
+    const int cps = slot / 16;
+    int span = 0, nslot = 0;
+    for (int sp = 4; sp >= 2 && !span; --sp) {
+        int n = 1;
+        for (int i = 0; i < K; ++i) n *= sp;
+        if ((int64_t)n * (slot + 12) <= kTracebackSmem) {
+            span = sp;
+            nslot = n;
+        }
+    }
+    if (!span || cps > kTbThreads) {
+        walk_direct(P, io, smem, ws);
+        return;
+    }
+    int64_t *sstart = reinterpret_cast<int64_t *>(smem + (size_t)nslot * slot);  // per slot: block's global offset
+    unsigned *sbase = reinterpret_cast<unsigned *>(sstart + nslot);             // per slot: shared address of its byte 0
+    const int len_sum = P.len_sum;
+    while (true) {
+        __syncthreads();
+        if (ws.fail || at_origin(K, ws.x)) break;
+        int qlo[K], sst[K];
+        int n = 1;
+        for (int i = K - 1; i >= 0; --i) {
+            qlo[i] = max(0, ws.x[i] / E[i] - span + 1);
+            sst[i] = n;
+            n *= ws.x[i] / E[i] - qlo[i] + 1;
+        }
+        for (int sl = tid; sl < n; sl += kTbThreads) {  // each staged tile's block
+            int r = sl;
+            int64_t t = 0;
+            for (int i = 0; i < K; ++i) {
+                const int d = r / sst[i];
+                r -= d * sst[i];
+                t += (int64_t)(qlo[i] + d) * P.gstride[i];
+            }
+            const int64_t start = t * vol;
+            sstart[sl] = start & ~(int64_t)15;
+            sbase[sl] = smem_u32(smem + (size_t)sl * slot) + (unsigned)(start & 15);
+        }
+        __syncthreads();
+        {  // thread tid copies chunk tid % cps of every (kTbThreads / cps)-th block,
+           // where the block reaches it (never past the block's last 16-byte run)
+            const int ch = tid % cps, step = kTbThreads / cps;
+            for (int sl = tid / cps; sl < n && tid < step * cps; sl += step)
+                if (16 * ch < (int)(sbase[sl] & 15) + vol)
+                    cp_async_16(smem + (size_t)sl * slot + 16 * ch, P.tb + sstart[sl] + 16 * ch);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (tid == 0) {
+            int x[K], c[K], q[K];
+            int loc = 0, sl = 0;
+            for (int i = 0; i < K; ++i) {
+                x[i] = ws.x[i];
+                q[i] = x[i] / E[i];
+                c[i] = x[i] - q[i] * E[i];
+                loc += c[i] * lst[i];
+                sl += (q[i] - qlo[i]) * sst[i];
+            }
+            unsigned base = sbase[sl];
+            int ncols = ws.ncols;
+            const int before = ncols;
+            bool fail = false;
+            while (!at_origin(K, x)) {
+                const int m = lds_u8(base + (unsigned)loc);
+                int zero = 0;
+                for (int i = 0; i < K; ++i) zero |= (x[i] == 0) << i;
+                if (m == 0 || (m >> K) != 0 || (m & zero) != 0 || ncols >= len_sum) {
+                    fail = true;
+                    break;
+                }
+                stg_u8(io.masks + ncols, m);
+                ++ncols;
+                bool out = false, cross = false;
+                for (int i = 0; i < K; ++i)
+                    if ((m >> i) & 1) {
+                        --x[i];
+                        if (c[i] > 0) {
+                            --c[i];
+                            loc -= lst[i];
+                        } else {  // into the tile below along axis i
+                            c[i] = E[i] - 1;
+                            loc += (E[i] - 1) * lst[i];
+                            --q[i];
+                            sl -= sst[i];
+                            cross = true;
+                            out = out || q[i] < qlo[i];
+                        }
+                    }
+                if (out) break;
+                if (cross) base = sbase[sl];
+            }
+            if (ncols == before && !at_origin(K, x)) fail = true;  // a region must advance the walk
+            for (int i = 0; i < K; ++i) ws.x[i] = x[i];
+            ws.ncols = ncols;
+            if (fail) ws.fail = 1;
+        }
+    }
+}
+
 // Score of the recorded path, by the whole CTA: sum over columns of
 // u*|m| + sum over moved pairs (sub - 2 gap), each column at the position the
 // suffix of later moves (earlier in the record) gives it.
@@ -494,6 +611,16 @@ __global__ void __launch_bounds__(kTbThreads) traceback_kernel(const ProblemDesc
         walk_boxes<2>(P, io, smem, ws);
     else if (K == 3)
         walk_boxes<3>(P, io, smem, ws);
+    else if (P.tb_layout == 2 && K == 4)
+        walk_tiles<4>(P, io, smem, ws);
+    else if (P.tb_layout == 2 && K == 5)
+        walk_tiles<5>(P, io, smem, ws);
+    else if (P.tb_layout == 2 && K == 6)
+        walk_tiles<6>(P, io, smem, ws);
+    else if (P.tb_layout == 2 && K == 7)
+        walk_tiles<7>(P, io, smem, ws);
+    else if (P.tb_layout == 2 && K == 8)
+        walk_tiles<8>(P, io, smem, ws);
     else
         walk_direct(P, io, smem, ws);
     __syncthreads();
