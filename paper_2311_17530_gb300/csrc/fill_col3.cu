@@ -244,7 +244,7 @@ struct C3Col {
 // trip per batch). Loads are 16-byte pairs of entries: an F0 row (32 entries) is
 // read by half a warp, an F1 row (WR entries) by WR / 2 lanes.
 __device__ void c3_stager(C3Smem &sm, const C3Col &cc, int lane, const LaunchDesc &L) {
-    constexpr int SB = 16;                       // rows per batch
+    constexpr int SB = 8;                        // rows per batch (one block: measured best)
     constexpr int NL0 = SB / 2;                  // F0 loads per lane and batch (2 rows per load)
     constexpr int LPR1 = c3::WR / 2;             // lanes per F1 row
     constexpr int RPI1 = 32 / LPR1;              // F1 rows per load
