@@ -1,0 +1,49 @@
+"""Host logic of bench.py that the JSON line rests on: the traffic figure is only
+reported for the fill kernel the committed ncu summary was taken on, keyed by a
+digest of the kernel's code (its own file and the headers it includes) that
+ignores comments and blank lines but not code."""
+import json
+import os
+import shutil
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _with_sources(tmp_path, edit):
+    """A copy of the kernel sources (and the header they include) with `edit` applied to fill_col3.cu."""
+    pkg = tmp_path / "paper_2311_17530_gb300"
+    shutil.copytree(os.path.join(ROOT, "paper_2311_17530_gb300", "csrc"), pkg / "csrc")
+    shutil.copytree(os.path.join(ROOT, "include"), tmp_path / "include")
+    f = pkg / "csrc" / "fill_col3.cu"
+    f.write_text(edit(f.read_text()))
+    return str(tmp_path)
+
+
+def test_digest_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    base = bench.kernel_source_digest("fill_col3")
+    root_c = _with_sources(tmp_path / "c", lambda s: s.replace("namespace msadp {", "// a new comment\n\n/* and a block */\nnamespace msadp {", 1))
+    monkeypatch.setattr(bench, "ROOT", root_c)
+    assert bench.kernel_source_digest("fill_col3") == base
+    root_x = _with_sources(tmp_path / "x", lambda s: s.replace("constexpr int SB = 8;", "constexpr int SB = 16;", 1))
+    monkeypatch.setattr(bench, "ROOT", root_x)
+    assert bench.kernel_source_digest("fill_col3") != base
+
+
+def test_traffic_only_for_matching_digest(tmp_path, monkeypatch):
+    rec = {"fill_col3:k3_protein": {"source_digest": bench.kernel_source_digest("fill_col3"),
+                                    "dram_bytes_per_launch": 123}}
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.json").write_text(json.dumps(rec))
+    pkg = tmp_path / "paper_2311_17530_gb300"
+    shutil.copytree(os.path.join(ROOT, "paper_2311_17530_gb300", "csrc"), pkg / "csrc")
+    shutil.copytree(os.path.join(ROOT, "include"), tmp_path / "include")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic("k3_protein", "fill_col3") == 123
+    assert bench.measured_traffic("k4_dna", "fill_tiles") is None
+    rec["fill_col3:k3_protein"]["source_digest"] = "0" * 16
+    (prof / "traffic.json").write_text(json.dumps(rec))
+    assert bench.measured_traffic("k3_protein", "fill_col3") is None
