@@ -206,24 +206,38 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
         std::sort(key.begin(), key.end());
         hp.order.resize(nt);
         for (int64_t t = 0; t < nt; ++t) hp.order[t] = (uint64_t)key[t].second;
+        // the key is (WR + U) (a + b): waves of equal a + b, contiguous in the order
+        static_assert(c3::WR == 32, "column waves by a + b");
+        hp.wave_start.assign((size_t)(hp.G[0] + hp.G[1]), 0);
+        for (int64_t t = 0; t < nt; ++t) hp.wave_start[(size_t)(t / hp.G[1] + t % hp.G[1] + 1)]++;
+        for (size_t w = 1; w < hp.wave_start.size(); ++w) hp.wave_start[w] += hp.wave_start[w - 1];
         return MSA_OK;
     }
 
-    // ticket order: by wave, then by linear tile index (counting sort)
+    // ticket order: by wave, then by linear tile index (counting sort); the wave
+    // of each tile follows its grid coordinates, stepped like an odometer (last
+    // axis fastest) instead of decoded from the linear index
     std::vector<int64_t> cnt(hp.waves + 1, 0);
     std::vector<int32_t> wave_of(nt);
-    for (int64_t t = 0; t < nt; ++t) {
-        int64_t rem = t;
+    {
+        int c[MSA_MAX_K] = {};
         int w = 0;
-        for (int i = 0; i < k; ++i) {
-            const int64_t c = rem / hp.gstride[i];
-            rem -= c * hp.gstride[i];
-            w += (int)c;
+        for (int64_t t = 0; t < nt; ++t) {
+            wave_of[t] = w;
+            cnt[w + 1]++;
+            for (int i = k - 1; i >= 0; --i) {
+                if (c[i] + 1 < hp.G[i]) {
+                    ++c[i];
+                    ++w;
+                    break;
+                }
+                w -= c[i];
+                c[i] = 0;
+            }
         }
-        wave_of[t] = w;
-        cnt[w + 1]++;
     }
     for (int w = 0; w < hp.waves; ++w) cnt[w + 1] += cnt[w];
+    hp.wave_start = cnt;
     hp.order.assign(nt, 0);
     for (int64_t t = 0; t < nt; ++t) hp.order[cnt[wave_of[t]]++] = (uint64_t)t;
     return MSA_OK;

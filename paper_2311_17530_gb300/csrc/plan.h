@@ -40,6 +40,7 @@ struct HostPlan {
     int32_t w_corner = 0;
     int32_t len_sum = 0;
     std::vector<uint64_t> order;   // ticket -> tile linear index (problem bits added by callers)
+    std::vector<int64_t> wave_start;  // order[wave_start[w] .. wave_start[w + 1]) is wave w (tile index sum)
 };
 
 // Tile (or column) extents the planner uses for these lengths, kernel and edge.

@@ -509,39 +509,21 @@ int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg
             max_ncode = std::max<int64_t>(max_ncode, r->hp.len_sum);
         }
         // merged ticket order: every request's own topological order, interleaved
-        // by wave (tiles) or by start-time estimate (columns)
-        struct Key {
-            int64_t key;
-            int32_t p;
-            int64_t tile;
-        };
-        std::vector<Key> keys;
-        keys.reserve((size_t)g.tickets);
-        for (int j = 0; j < g.count; ++j) {
-            const HostPlan &hp = batch[g.first + j]->hp;
-            for (int64_t t = 0; t < hp.ntiles; ++t) {
-                const int64_t tile = (int64_t)hp.order[t];
-                int64_t key;
-                if (hp.kernel == kKernelCol3) {
-                    key = (tile / hp.G[1]) * (c3::WR + c3::U) + (tile % hp.G[1]) * (32 + c3::U);
-                } else {
-                    int64_t rem = tile;
-                    key = 0;
-                    for (int a = 0; a < hp.k; ++a) {
-                        const int64_t c = rem / hp.gstride[a];
-                        rem -= c * hp.gstride[a];
-                        key += c;
-                    }
-                }
-                keys.push_back({key, j, t});
-            }
-        }
-        std::stable_sort(keys.begin(), keys.end(), [](const Key &a, const Key &b) { return a.key < b.key; });
+        // wave by wave (tiles: equal tile index sum; columns: equal a + b), each
+        // wave taking the requests in batch order -- one pass over the tickets
         uint64_t *ord = reinterpret_cast<uint64_t *>(H + g.order_off);
-        for (size_t t = 0; t < keys.size(); ++t) {
-            const HostPlan &hp = batch[g.first + keys[t].p]->hp;
-            ord[t] = ((uint64_t)keys[t].p << 32) | hp.order[keys[t].tile];
-        }
+        size_t nw = 0;
+        for (int j = 0; j < g.count; ++j) nw = std::max(nw, batch[g.first + j]->hp.wave_start.size());
+        size_t pos = 0;
+        for (size_t w = 0; w + 1 < nw; ++w)
+            for (int j = 0; j < g.count; ++j) {
+                const HostPlan &hp = batch[g.first + j]->hp;
+                if (w + 1 >= hp.wave_start.size()) continue;
+                for (int64_t t = hp.wave_start[w]; t < hp.wave_start[w + 1]; ++t)
+                    ord[pos++] = ((uint64_t)j << 32) | hp.order[(size_t)t];
+            }
+        if (pos != (size_t)g.tickets) return set_error(MSA_EINVAL, "ticket merge: %zu of %lld tickets", pos,
+                                                        (long long)g.tickets);
         g.grid = persistent_grid(g.k, g.kernel, g.tickets, g.maxA, g.edge);  // no occupancy query in a capture
     }
     bool col3 = false;
