@@ -3,6 +3,7 @@ and the tile shape the planner reports for a chosen edge (section 3.2's
 partition size S; Eq. 2 and 3 count the waves and tiles of the resulting grid)."""
 import math
 import os
+import shutil
 import subprocess
 
 import pytest
@@ -63,7 +64,6 @@ def test_planner_refuses_tensors_beyond_32_bit_tile_blocks():
 
 
 def _nvcc():
-    import shutil
     for c in ("/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
         if c and os.path.exists(c):
             return c
@@ -77,6 +77,19 @@ def test_padded_tile_layout_is_a_bijection(tmp_path):
     exe = tmp_path / "tile_geometry_check"
     subprocess.check_call([_nvcc(), "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-I", CSRC, "-I",
                            os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "tile_geometry_check.cu"),
+                           "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout
+
+
+@pytest.mark.skipif(shutil.which("g++") is None, reason="needs g++")
+def test_planner_ticket_order_is_by_wave(tmp_path):
+    # every tile once, by wave (tile index sum, decoded by division) and by
+    # increasing linear index within a wave; wave offsets; column plans by a + b
+    exe = tmp_path / "plan_order_check"
+    cuda_inc = "/usr/local/cuda/include"
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"), "-I", cuda_inc,
+                           os.path.join(ROOT, "tests", "plan_order_check.cpp"), os.path.join(CSRC, "plan.cpp"),
                            "-o", str(exe)])
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout
