@@ -138,6 +138,8 @@ KERNEL_SOURCES = {
                   "csrc/device_common.cuh", "../include/msadp.h"],
     "fill_tiles": ["csrc/fill_tiles.cuh"] + [f"csrc/fill_tiles_k{k}.cu" for k in range(2, 9)] +
                   ["csrc/internal.h", "csrc/device_common.cuh", "../include/msadp.h"],
+    "fill_band2": ["csrc/fill_band2.cu", "csrc/api_internal.h", "csrc/plan.h", "csrc/internal.h",
+                   "csrc/device_common.cuh", "../include/msadp.h"],
 }
 
 
@@ -430,7 +432,7 @@ def run_gb300(args, rank, world, local):
                "h2d_bytes_per_step": total_len + p.subst.size * 4,
                "d2h_bytes_per_step": 16 + total_len, "ms_per_step": 1e3 * tot / args.steps}
 
-    kernel = "fill_tiles" if info.fill_kernel == 1 else "fill_col3"
+    kernel = {1: "fill_tiles", 2: "fill_col3", 3: "fill_band2"}[int(info.fill_kernel)]
     ops = alg_ops_per_cell(p.k) * p.cells
     achieved = ops / (fill_ms / 1e3) / 1e12
     peak = alu_peak_tiops(sms)

@@ -92,7 +92,8 @@ int msa_set_stream(void *stream);
  *   "use_graphs"        1: the serving loop replays captured CUDA graphs (default 1)
  *   "batching"          1: serve by continuous batching; 0: one plain launch per
  *                       request, in arrival order (default 1)
- *   "fill_kernel"       0: automatic; 1: generic tile kernel; 2: k=3 column kernel
+ *   "fill_kernel"       0: automatic; 1: generic tile kernel; 2: k=3 column kernel;
+ *                       3: k=2 band kernel
  *   "timing"            1: msa_plan_execute records per-stage CUDA events (default 0)
  *   "test_withhold_tile" test hook: the tile with this ticket never publishes its
  *                       completion, so its dependants time out (default -1: off)
@@ -118,10 +119,12 @@ typedef struct msa_plan_info {
     int32_t tile_extent[MSA_MAX_K];
     int64_t tiles;
     int32_t waves;              /* tile hyperplanes (section 3.1, Eq. 2) */
-    int32_t fill_kernel;        /* 1 generic tile kernel, 2 k=3 column kernel */
+    int32_t fill_kernel;        /* 1 generic tile kernel, 2 k=3 column kernel, 3 k=2 band kernel */
     void   *d_tb;               /* device pointer of the uint8 traceback tensor: row-major with
-                                   tb_strides for the tile kernel; for the k=3 column kernel a
-                                   column-blocked layout (msa_plan_read_tb returns row-major) */
+                                   tb_strides for the tile kernel (k <= 3) and the band kernel;
+                                   tile-major for the tile kernel at k >= 4; for the k=3 column
+                                   kernel a column-blocked layout (msa_plan_read_tb returns
+                                   row-major) */
 } msa_plan_info;
 
 /* Result block written on the device by msa_plan_execute. */
@@ -263,10 +266,11 @@ int msa_tile_shape(int k, const int32_t *lens, int32_t *out_extent, int32_t *out
 /*
  * Tile edge of the generic kernel for k (the paper's partition size S, section
  * 3.2): the tile spans `edge` cells on every axis (k = 2: edge x 2*edge). Only
- * compiled edges are accepted (k=2: 16 32 64; k=3: 8 12 16; k=4: 4 6 8; k=5: 3 4
+ * compiled edges are accepted (k=2: 16 32 64; k=3: 8 12 16; k=4: 4 5 6; k=5: 3 4
  * 5; k=6: 2 3 4; k=7: 2 3; k=8: 2); 0 restores the default (for k = 3 also the
- * automatic choice of the column kernel where it fits). Later plans and serving
- * batches use the setting. Host-only, thread-safe.
+ * automatic choice of the column kernel where it fits, for k = 2 of the band
+ * kernel). Later plans and serving batches use the setting. Host-only,
+ * thread-safe.
  */
 int msa_set_tile_edge(int k, int32_t edge);
 int msa_get_tile_edge(int k, int32_t *out_edge);
@@ -280,19 +284,19 @@ int msa_get_tile_edge(int k, int32_t *out_edge);
 typedef struct msa_tuning {
     int32_t k;
     int32_t ncand;                                   /* candidates timed */
-    int32_t cand_kernel[MSA_MAX_TUNING_CANDIDATES];  /* 1 generic tiles, 2 k=3 column kernel */
-    int32_t cand_edge[MSA_MAX_TUNING_CANDIDATES];    /* tile edge (0 for the column kernel) */
+    int32_t cand_kernel[MSA_MAX_TUNING_CANDIDATES];  /* 1 generic tiles, 2 k=3 column, 3 k=2 band */
+    int32_t cand_edge[MSA_MAX_TUNING_CANDIDATES];    /* tile edge (0 for the column and band kernels) */
     float cand_ms[MSA_MAX_TUNING_CANDIDATES];        /* mean ms of one execution (encode+fill+traceback) */
     int32_t best;                                    /* index of the chosen candidate */
 } msa_tuning;
 
 /*
- * Time every compiled tile edge for k (and, for k = 3, the column kernel) on a
- * synthetic problem with these lengths over an alphabet of alphabet_size
- * letters: one warm-up and `repeats` executions each, on the library stream. The
- * fastest becomes the choice for k (msa_set_tile_edge, and for k = 3 whether the
- * automatic kernel choice takes the column kernel). Allocates device memory;
- * synchronous.
+ * Time every compiled tile edge for k (and the column kernel for k = 3, the band
+ * kernel for k = 2) on a synthetic problem with these lengths over an alphabet of
+ * alphabet_size letters: one warm-up and `repeats` executions each, on the
+ * library stream. The fastest becomes the choice for k (msa_set_tile_edge, and
+ * for k = 2, 3 whether the automatic kernel choice takes the band or column
+ * kernel). Allocates device memory; synchronous.
  */
 int msa_autotune(int k, const int32_t *lens, int alphabet_size, int32_t repeats, msa_tuning *out);
 

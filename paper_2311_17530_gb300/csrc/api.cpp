@@ -117,19 +117,23 @@ int device_sm_count() {
 int persistent_grid(int k, int kernel, int64_t units, int A, int edge) {
     // resident CTAs per SM, cached per (kernel, k, alphabet size or tile edge)
     static std::mutex mu;
-    static int cache[3][MSA_MAX_K + 1][MSA_MAX_ALPHABET + 1] = {};
+    static int cache[4][MSA_MAX_K + 1][MSA_MAX_ALPHABET + 1] = {};
     int c;
     {
         std::lock_guard<std::mutex> g(mu);
         int &slot = cache[kernel][k][kernel == kKernelCol3 ? A : (edge & 31)];
         if (!slot) {
-            slot = kernel == kKernelCol3 ? fill_col3_ctas_per_sm(col3_smem_bytes(A)) : fill_tiles_ctas_per_sm(k, edge);
+            slot = kernel == kKernelCol3    ? fill_col3_ctas_per_sm(col3_smem_bytes(A))
+                   : kernel == kKernelBand2 ? fill_band2_ctas_per_sm()
+                                            : fill_tiles_ctas_per_sm(k, edge);
             if (slot <= 0) slot = 1;
         }
         c = slot;
     }
-    // the tile kernel takes one unit per warp, the column kernel one per CTA
-    const int per_cta = kernel == kKernelCol3 ? 1 : std::max(1, fill_tiles_warps_per_cta(k, edge));
+    // the tile and band kernels take one unit per warp, the column kernel one per CTA
+    const int per_cta = kernel == kKernelCol3    ? 1
+                      : kernel == kKernelBand2 ? fill_band2_warps_per_cta()
+                                               : std::max(1, fill_tiles_warps_per_cta(k, edge));
     int64_t need = (units + per_cta - 1) / per_cta;
     int64_t g = (int64_t)c * device_sm_count();
     if (need < g) g = need;
@@ -223,8 +227,9 @@ cudaError_t clear_faces(const HostPlan &hp, const PlanPointers &pp, cudaStream_t
 }
 
 int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t s) {
-    cudaError_t e = hp.kernel == kKernelCol3 ? launch_fill_col3(L, grid, col3_smem_bytes(hp.A), s)
-                                             : launch_fill_tiles(hp.k, hp.edge, L, grid, s);
+    cudaError_t e = hp.kernel == kKernelCol3    ? launch_fill_col3(L, grid, col3_smem_bytes(hp.A), s)
+                  : hp.kernel == kKernelBand2 ? launch_fill_band2(L, grid, s)
+                                              : launch_fill_tiles(hp.k, hp.edge, L, grid, s);
     return e == cudaSuccess ? MSA_OK : cuda_error(e, "fill kernel launch");
 }
 
@@ -277,7 +282,7 @@ int msa_config(const char *key, int64_t value) {
     } else if (!strcmp(key, "batching")) {
         s.batching = value ? 1 : 0;
     } else if (!strcmp(key, "fill_kernel")) {
-        if (value < 0 || value > 2) return set_error(MSA_EINVAL, "fill_kernel must be 0, 1 or 2");
+        if (value < 0 || value > 3) return set_error(MSA_EINVAL, "fill_kernel must be 0, 1, 2 or 3");
         s.fill_kernel = value;
     } else if (!strcmp(key, "timing")) {
         s.timing = value ? 1 : 0;

@@ -210,6 +210,9 @@ int fill_tiles_ctas_per_sm(int k, int edge);
 int fill_tiles_warps_per_cta(int k, int edge);
 cudaError_t launch_fill_col3(const LaunchDesc &L, int grid, int smem, cudaStream_t s);
 int fill_col3_ctas_per_sm(int smem);
+cudaError_t launch_fill_band2(const LaunchDesc &L, int grid, cudaStream_t s);
+int fill_band2_ctas_per_sm();
+int fill_band2_warps_per_cta();
 int col3_smem_bytes(int alphabet_size);
 cudaError_t launch_traceback(const ProblemDesc *d_probs, int nprob, const int32_t *err,
                              const IODesc *io_array, IODesc io_single, cudaStream_t s);

@@ -22,6 +22,7 @@ namespace {
 std::mutex g_tune_mu;
 int g_edge[MSA_MAX_K + 1] = {};  // 0: default edge
 bool g_k3_tiles = false;
+bool g_k2_tiles = false;
 }  // namespace
 
 int tile_edge_for(int k) {
@@ -47,8 +48,19 @@ void set_prefer_tiles_k3(bool v) {
     g_k3_tiles = v;
 }
 
+bool prefer_tiles_k2() {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    return g_k2_tiles;
+}
+
+void set_prefer_tiles_k2(bool v) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_k2_tiles = v;
+}
+
 int choose_kernel(int k, const int32_t *lens, int A, int requested) {
     if (requested == kKernelTiles) return kKernelTiles;
+    if (k == 2 && (requested == kKernelBand2 || (requested == kKernelAuto && !prefer_tiles_k2()))) return kKernelBand2;
     if (col3_fits(k, lens, A) && (requested == kKernelCol3 || !prefer_tiles_k3())) return kKernelCol3;
     return kKernelTiles;
 }
@@ -58,6 +70,11 @@ void tile_extents(int k, const int32_t *lens, int kernel, int edge, int32_t *E) 
         E[0] = c3::WR;
         E[1] = 32;
         E[2] = lens[2] + 1;
+        return;
+    }
+    if (kernel == kKernelBand2) {  // bands of 32 rows spanning every column
+        E[0] = 32;
+        E[1] = lens[1] + 1;
         return;
     }
     for (int i = 0; i < k; ++i) E[i] = tile_ext(k, edge, i);
@@ -183,6 +200,11 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
     if (!score_and_traceback_layout(hp)) {
         err = "score scratch beyond 32-bit element offsets";
         return MSA_ETOOBIG;
+    }
+    if (hp.kernel == kKernelBand2) {
+        // scores: only each band's last row, the face the band below reads
+        hp.face0_stride = round_up64(hp.rho[1], 32);
+        hp.qelems = hp.ntiles * hp.face0_stride;
     }
 
     if (hp.kernel == kKernelCol3) {

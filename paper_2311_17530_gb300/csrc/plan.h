@@ -10,7 +10,7 @@
 
 namespace msadp {
 
-enum FillKernel { kKernelAuto = 0, kKernelTiles = 1, kKernelCol3 = 2 };
+enum FillKernel { kKernelAuto = 0, kKernelTiles = 1, kKernelCol3 = 2, kKernelBand2 = 3 };
 
 struct HostPlan {
     int k = 0;
@@ -47,12 +47,15 @@ struct HostPlan {
 void tile_extents(int k, const int32_t *lens, int kernel, int edge, int32_t *E);
 
 // Tuned choices per k (process-wide, thread-safe): the generic kernel's tile
-// edge (0 restores the default) and, for k = 3, whether the automatic choice
-// prefers the generic kernel over the column kernel.
+// edge (0 restores the default) and, for k = 3 (k = 2), whether the automatic
+// choice prefers the generic kernel over the column (band) kernel.
 int tile_edge_for(int k);
 int set_tile_edge(int k, int edge);
 bool prefer_tiles_k3();
 void set_prefer_tiles_k3(bool v);
+// k = 2: whether the automatic choice prefers the generic kernel over the band kernel
+bool prefer_tiles_k2();
+void set_prefer_tiles_k2(bool v);
 
 // Score scratch and traceback layouts from k, rho, the kernel, tile extents and
 // tile count (row-major, or tile-major for the generic kernel at k >= 4).

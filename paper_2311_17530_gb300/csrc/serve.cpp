@@ -565,8 +565,9 @@ int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg
         L.nprob = g.count;
         L.tab_ints = g.maxA * (g.maxA + 1) * 32;
         L.epoch = epoch_;
-        e = g.kernel == kKernelCol3 ? launch_fill_col3(L, g.grid, col3_smem_bytes(g.maxA), s)
-                                    : launch_fill_tiles(g.k, g.edge, L, g.grid, s);
+        e = g.kernel == kKernelCol3    ? launch_fill_col3(L, g.grid, col3_smem_bytes(g.maxA), s)
+          : g.kernel == kKernelBand2 ? launch_fill_band2(L, g.grid, s)
+                                     : launch_fill_tiles(g.k, g.edge, L, g.grid, s);
     }
     if (e == cudaSuccess) e = launch_traceback(ddesc, n, &dstate[0].err, dio, IODesc{}, s);
     if (e == cudaSuccess)

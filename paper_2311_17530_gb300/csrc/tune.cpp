@@ -1,6 +1,7 @@
 // Autotuner of the tile shape: the paper fixes its partition size S by hand
 // (section 3.2's example uses S = 3); here each k has a few compiled tile edges
-// (tile_edge_candidate) and, for k = 3, the column kernel. msa_autotune times
+// (tile_edge_candidate) and, for k = 3, the column kernel (k = 2: the band
+// kernel). msa_autotune times
 // every candidate on a synthetic problem of the caller's shape -- plan creation,
 // then repeated executions of encode, fill and traceback between CUDA events --
 // and makes the fastest the choice for k in every later plan and serving batch.
@@ -68,6 +69,7 @@ int msa_set_tile_edge(int k, int32_t edge) {
     if (set_tile_edge(k, edge) != MSA_OK)
         return set_error(MSA_EINVAL, "tile edge %d is not compiled for k=%d", edge, k);
     if (k == 3 && edge == 0) set_prefer_tiles_k3(false);  // defaults: the column kernel where it fits
+    if (k == 2 && edge == 0) set_prefer_tiles_k2(false);  // defaults: the band kernel
     return MSA_OK;
 }
 
@@ -124,6 +126,7 @@ int msa_autotune(int k, const int32_t *lens, int alphabet_size, int32_t repeats,
     for (int i = 0; i < kMaxTileEdges; ++i)
         if (tile_edge_candidate(k, i) > 0) cands.push_back({kKernelTiles, tile_edge_candidate(k, i)});
     if (k == 3 && choose_kernel(k, lens, alphabet_size, kKernelCol3) == kKernelCol3) cands.push_back({kKernelCol3, 0});
+    if (k == 2) cands.push_back({kKernelBand2, 0});
     int best = -1;
     for (const Cand &c : cands) {
         if (out->ncand >= MSA_MAX_TUNING_CANDIDATES) break;
@@ -143,8 +146,10 @@ int msa_autotune(int k, const int32_t *lens, int alphabet_size, int32_t repeats,
     if (out->cand_kernel[best] == kKernelTiles) {
         set_tile_edge(k, out->cand_edge[best]);
         if (k == 3) set_prefer_tiles_k3(true);
+        if (k == 2) set_prefer_tiles_k2(true);
     } else {
-        set_prefer_tiles_k3(false);
+        if (k == 3) set_prefer_tiles_k3(false);
+        if (k == 2) set_prefer_tiles_k2(false);
         // the best generic edge stays the fallback for shapes the column kernel cannot take
         int bt = -1;
         for (int i = 0; i < out->ncand; ++i)

@@ -292,11 +292,12 @@ def msa_get_tile_edge(k: int) -> int:
 
 
 def msa_autotune(lens: Sequence[int], alphabet_size: int, repeats: int = 3) -> dict:
-    """Time the compiled tile shapes (and the k=3 column kernel) for this shape; the
+    """Time the compiled tile shapes (and the k=3 column or k=2 band kernel) for this shape; the
     fastest becomes the choice for k. Returns the candidates and the choice."""
     t = Tuning()
     _check(library().msa_autotune(len(lens), _i32(lens), int(alphabet_size), int(repeats), ctypes.byref(t)))
-    cands = [{"kernel": "column" if t.cand_kernel[i] == 2 else "tiles", "edge": int(t.cand_edge[i]),
+    names = {1: "tiles", 2: "column", 3: "band"}
+    cands = [{"kernel": names[int(t.cand_kernel[i])], "edge": int(t.cand_edge[i]),
               "ms": float(t.cand_ms[i])} for i in range(t.ncand)]
     return {"k": int(t.k), "lens": list(lens), "candidates": cands, "best": cands[t.best]}
 

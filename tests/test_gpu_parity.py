@@ -187,6 +187,40 @@ def test_k3_both_fill_kernels_block_boundaries(kernel):
         msa.msa_config("fill_kernel", 0)
 
 
+@pytest.mark.parametrize("kernel", [1, 3])
+def test_k2_tile_and_band_kernels_boundaries(kernel):
+    """k=2 through the generic tile kernel (1) and the band kernel (3): shapes
+    straddling the band kernel's 32-row bands and 32-column face blocks, empty
+    and single-row or single-column problems."""
+    msa.msa_config("fill_kernel", kernel)
+    try:
+        shapes = [(31, 31), (32, 32), (33, 33), (63, 95), (64, 1), (1, 64), (0, 50), (50, 0), (0, 0), (1, 1),
+                  (97, 33), (200, 180), (31, 500), (500, 31), (95, 96)]
+        for i, lens in enumerate(shapes):
+            p = inputs.random_problem(1900 + i, 2, list(lens),
+                                      alphabet=inputs.PROTEIN if i % 2 else inputs.DNA, related=i % 3 == 0)
+            with msa.Plan(2, p.lens, p.alphabet) as plan:
+                assert plan.info().fill_kernel == kernel
+            check_problem(p)
+    finally:
+        msa.msa_config("fill_kernel", 0)
+
+
+def test_k2_band_wait_timeout_is_reported_not_hung():
+    """A withheld band never publishes its face, so the band below times out."""
+    p = inputs.random_problem(7, 2, [100, 80])
+    with msa.Plan(2, p.lens, p.alphabet) as plan:
+        assert plan.info().fill_kernel == 3
+    msa.msa_config("spin_timeout_ms", 200)
+    msa.msa_config("test_withhold_tile", 0)
+    try:
+        assert run_plan(p)[2] == msa.MSA_ETIMEOUT
+    finally:
+        msa.msa_config("test_withhold_tile", -1)
+        msa.msa_config("spin_timeout_ms", 5000)
+    check_problem(p)
+
+
 def test_k3_auto_picks_column_kernel():
     p = inputs.k3_protein()
     with msa.Plan(3, [10, 10, 10], p.alphabet) as plan:
