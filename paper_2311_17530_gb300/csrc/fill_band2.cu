@@ -29,6 +29,10 @@ constexpr int kBandWarps = 8;  // warps per CTA, one band each
 
 __global__ void __launch_bounds__(kBandWarps * 32) fill_band2_kernel(const LaunchDesc L) {
     const int lane = threadIdx.x & 31;
+    // per warp: each lane's row of the pair table, transposed (entry b of lane l
+    // at b * 32 + l, so a step's 32 lookups hit 32 banks)
+    __shared__ int tabT[kBandWarps][MSA_MAX_ALPHABET * 32];
+    int *trow = tabT[threadIdx.x >> 5];
     while (true) {
         int t = 0, err = 0;
         if (lane == 0) {
@@ -58,25 +62,37 @@ __global__ void __launch_bounds__(kBandWarps * 32) fill_band2_kernel(const Launc
         const int i = band * 32 + lane;  // this lane's row x0
         const bool row_ok = i < rho0;
         const uint8_t *c1 = P.codes + P.cofs[1];
-        const int32_t *tab = P.tab;
         const int arow = (row_ok && i >= 1) ? (int)P.codes[P.cofs[0] + i - 1] * P.A : 0;
+        __syncwarp();
+        for (int b = 0; b < P.A; ++b) trow[b * 32 + lane] = __ldg(P.tab + arow + b);
+        __syncwarp();
         uint8_t *tbrow = P.tb + (int64_t)(row_ok ? i : 0) * P.tbstride[0];
         const bool publish = lane == 31 && (int64_t)t != L.withhold;
         int V = kNeg;        // this lane's value at its previous column
         int up_prev = kNeg;  // the cell above one column back: the diagonal predecessor
         int fblk = kNeg;     // lane q holds the band above's face at column 32 * block + q
+        int cblk = 0;        // lane q holds the residue code consumed at column 32 * block + q
+        int bj = 0;          // the code consumed at this lane's column (shifted along the lanes)
         unsigned pk = 0;     // traceback bytes of the current 4-column group
         bool ok = true;
         for (int s = 0; s < rho1 + 31; ++s) {
-            if (band > 0 && (s & 31) == 0 && s < rho1) {  // lane 0 enters block s / 32: stage the face
-                const int need = (s >> 5) + 1;
-                bool w = true;
-                if (lane == 0) w = wait_at_least(prog_in, need, L.err, L.spin_ns);
-                ok = __shfl_sync(kFull, w, 0);
-                if (!ok) break;
-                __syncwarp();
+            if ((s & 31) == 0 && s < rho1) {  // lane 0 enters block s / 32: stage its codes and face
                 const int col = s + lane;
-                fblk = col < rho1 ? __ldcg(face_in + col) : kNeg;
+                cblk = (col >= 1 && col < rho1) ? (int)c1[col - 1] : 0;
+                if (band > 0) {
+                    const int need = (s >> 5) + 1;
+                    bool w = true;
+                    if (lane == 0) w = wait_at_least(prog_in, need, L.err, L.spin_ns);
+                    ok = __shfl_sync(kFull, w, 0);
+                    if (!ok) break;
+                    __syncwarp();
+                    fblk = col < rho1 ? __ldcg(face_in + col) : kNeg;
+                }
+            }
+            {  // lane l's column s - l consumes the code lane l - 1 held a step ago
+                const int b0 = __shfl_sync(kFull, cblk, s & 31);
+                const int b = __shfl_up_sync(kFull, bj, 1);
+                bj = lane == 0 ? b0 : b;
             }
             const int from_face = __shfl_sync(kFull, fblk, s & 31);
             int up = __shfl_up_sync(kFull, V, 1);
@@ -91,7 +107,7 @@ __global__ void __launch_bounds__(kBandWarps * 32) fill_band2_kernel(const Launc
                     Vn = 0;  // H(0) = 0, no move
                 } else {
                     int acc = max(up, V);
-                    if (i >= 1 && j >= 1) acc = __viaddmax_s32(diag, __ldg(tab + arow + c1[j - 1]), acc);
+                    if (i >= 1 && j >= 1) acc = __viaddmax_s32(diag, trow[bj * 32 + lane], acc);
                     m = (i + 2 * j - acc) & 3;
                     Vn = acc + m;
                 }
