@@ -1,7 +1,8 @@
 // Host check of the planner's ticket order (compiled by tests/test_tile_edges_host.py):
-// for tile plans the order lists every tile once, by wave (sum of the tile's grid
-// coordinates, decoded here by division) and by increasing linear index within a
-// wave; for column plans by a + b; and wave_start marks where each wave begins.
+// for tile (and band) plans the order lists every tile once, by wave (sum of the
+// tile's grid coordinates, decoded here by division) and by increasing linear
+// index within a wave; for column plans by a + b; and wave_start marks where each
+// wave begins.
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -51,6 +52,8 @@ int main() {
                   l6[] = {7, 9, 8, 6, 9, 5}, l7[] = {4, 5, 3, 6, 2, 5, 4}, l8[] = {3, 2, 4, 3, 1, 2, 3, 2},
                   l3c[] = {700, 760, 800}, l0[] = {0, 0, 0};
     bad += check(2, l2, 20, 1, 32);
+    bad += check(2, l2, 20, 3, -1);  // band kernel: one ticket per 32-row band, in band order
+    bad += check(2, l0, 4, 3, -1);
     bad += check(3, l3, 20, 1, 12);
     bad += check(3, l3, 20, 2, -1);
     bad += check(3, l3c, 20, 2, -1);
