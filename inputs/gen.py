@@ -138,7 +138,7 @@ def related_family(rng: np.random.Generator, alphabet: str, lens: List[int],
 
 
 # --------------------------------------------------------------------------
-# The four single-problem workloads and the serving stream.
+# The single-problem workloads and the serving stream.
 # --------------------------------------------------------------------------
 
 def pr1(seed: int = 1) -> Problem:
@@ -175,8 +175,21 @@ def k6_protein(seed: int = 4, table_seed: int = 2) -> Problem:
     return Problem("k6_protein_18_24", seqs, PROTEIN, table, -6, seed)
 
 
+def k2_protein(seed: int = 6, table_seed: int = 2) -> Problem:
+    """k=2 protein pair, lengths 5000/4800 from one ancestor (sub 0.2, indel 0.05).
+
+    The pairwise case of the method (section 2, Eq. 1), sized so one problem
+    spans 157 bands of 32 rows. Uses the substitution table of :func:`k3_protein`.
+    """
+    table = protein_table(np.random.default_rng(table_seed))
+    rng = np.random.default_rng(seed)
+    seqs = related_family(rng, PROTEIN, [5000, 4800], 0.2, 0.05)
+    return Problem("k2_protein_5000_4800", seqs, PROTEIN, table, -6, seed)
+
+
 WORKLOADS = {
     "pr1": pr1,
+    "k2_protein": k2_protein,
     "k3_protein": k3_protein,
     "k4_dna": k4_dna,
     "k6_protein": k6_protein,

@@ -111,7 +111,7 @@ def test_plan_reuse_is_deterministic():
     np.testing.assert_array_equal(a[3], b[3])
 
 
-@pytest.mark.parametrize("name", ["pr1", "k3_protein", "k4_dna", "k6_protein"])
+@pytest.mark.parametrize("name", ["pr1", "k2_protein", "k3_protein", "k4_dna", "k6_protein"])
 def test_full_size_workloads_against_stored_oracle_values(name):
     """Full-size workloads: score, alignment and sampled traceback bytes against
     values written by tests/golden/make_golden.py (oracle only)."""
