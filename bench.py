@@ -300,6 +300,37 @@ def run_serving(n: int):
             "speedup_closed_loop": batched["alignments_per_s"] / plain["alignments_per_s"], "poisson_sweep": sweep}
 
 
+def _oracle_warm(_: int) -> int:
+    import oracle
+    oracle.build()
+    return os.getpid()
+
+
+def _oracle_serving_request(i: int) -> int:
+    import oracle
+    p = inputs.serving_request(i)
+    oracle.align_problem(p)
+    return p.cells
+
+
+def serving_cpu_baseline(n: int, procs: int = 0):
+    """The oracle on the first ``n`` requests of the serving stream, one request
+    per task on ``procs`` spawned worker processes (default: every host core),
+    timed after the workers have started and loaded the oracle."""
+    import multiprocessing as mp
+    procs = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")  # no fork of a process that holds a CUDA context
+    with ctx.Pool(procs) as pool:
+        pool.map(_oracle_warm, range(procs), chunksize=1)
+        t0 = time.perf_counter()
+        cells = sum(pool.imap_unordered(_oracle_serving_request, range(n), chunksize=1))
+        dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "alignments/s", "cores": procs, "kind": "oracle",
+            "cells_per_s": cells / dt,
+            "sample": f"oracle on requests 0..{n - 1} of the serving stream, one request per task, "
+                      f"{procs} processes ({dt:.1f} s)"}
+
+
 def max_over_ranks(x: float, dist, device) -> float:
     """The largest value of x over all ranks (the job's time is its slowest rank's)."""
     if dist is None:
@@ -470,6 +501,11 @@ def run_gb300(args, rank, world, local):
     serving = None
     if world == 1 and not args.no_serving:
         serving = run_serving(args.serve_requests)
+        if rank == 0 and not args.no_cpu_baseline:
+            try:
+                serving["cpu_baseline"] = serving_cpu_baseline(args.serve_cpu_requests)
+            except Exception as exc:  # the GPU figures stand without it
+                serving["cpu_baseline"] = {"error": f"{type(exc).__name__}: {exc}"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -511,6 +547,8 @@ def main():
     ap.add_argument("--tile-edge", type=int, default=0, help="generic tile kernel with this tile edge")
     ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving stream")
     ap.add_argument("--cpu-cells", type=float, default=1.2e8, help="cells of the cpu_baseline sample")
+    ap.add_argument("--serve-cpu-requests", type=int, default=320,
+                    help="serving-stream requests the oracle runs on every host core (serving cpu_baseline)")
     ap.add_argument("--ref-cells", type=float, default=5e7, help="cells per step of --impl reference")
     args = ap.parse_args()
     rank, world, local = dist_setup()

@@ -1,7 +1,8 @@
 """Host logic of bench.py that the JSON line rests on: the traffic figure is only
 reported for the fill kernel the committed ncu summary was taken on, keyed by a
 digest of the kernel's code (its own file and the headers it includes) that
-ignores comments and blank lines but not code."""
+ignores comments and blank lines but not code; and the serving baseline that
+runs the oracle on spawned worker processes."""
 import json
 import os
 import shutil
@@ -47,3 +48,12 @@ def test_traffic_only_for_matching_digest(tmp_path, monkeypatch):
     rec["fill_col3:k3_protein"]["source_digest"] = "0" * 16
     (prof / "traffic.json").write_text(json.dumps(rec))
     assert bench.measured_traffic("k3_protein", "fill_col3") is None
+
+
+def test_serving_cpu_baseline_runs_on_spawned_workers():
+    """The serving baseline: the oracle on a prefix of the request stream, one
+    request per task, on spawned processes."""
+    r = bench.serving_cpu_baseline(3, procs=2)
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["unit"] == "alignments/s"
+    assert r["value"] > 0 and r["cells_per_s"] > 0
+    assert "requests 0..2" in r["sample"]
