@@ -151,8 +151,7 @@ size_t plan_layout(const HostPlan &hp, char *base, PlanPointers *pp, size_t *res
         return base ? base + o : nullptr;
     };
     char *hdr = take(sizeof(LaunchState));
-    const int64_t nflags = hp.kernel == kKernelCol3 ? hp.ntiles : hp.ntiles;
-    char *done = take((size_t)nflags * 4);
+    char *done = take((size_t)hp.ntiles * 4);  // one completion counter per ticket
     *reset_bytes = off;
     char *order = take((size_t)hp.ntiles * 8);
     char *prob = take(sizeof(ProblemDesc));
