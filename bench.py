@@ -4,8 +4,8 @@
 One step = the whole hot path over one problem: encode residues + scale the pair
 table, fill the k-dimensional tensor, trace back (hot-path steps a1-a5). The
 default workload is k=3 protein 700/760/800 (427,302,261 cells). Its working set
-(2.1 GB of scores and traceback bytes) is far larger than the 129 MB L2, so no
-L2 flush is needed between steps; a workload whose traceback tensor fits in L2
+(0.65 GB of traceback bytes and faces written per step) is far larger than the
+129 MB L2, so no L2 flush is needed between steps; a workload whose traceback tensor fits in L2
 (the k=2 pair, the 128^3 case) is timed one step at a time, with a write of
 twice the L2 size before each step, outside the timed events.
 
