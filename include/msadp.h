@@ -80,8 +80,10 @@ int msa_align(int k, const char *const *seqs, const int32_t *lens, const char *a
 /* Thread-local description of the last failure in this thread ("" if none). */
 const char *msa_last_error(void);
 
-/* Stream (a cudaStream_t, may be NULL for the legacy default stream) used by
-   msa_align and by the serving loop for launches made from this thread on. */
+/* Stream (a cudaStream_t, may be NULL for the legacy default stream) that
+   msa_align and msa_autotune launch on from now on, in every thread (default: a
+   non-blocking stream the library creates). The serving loop keeps its own
+   streams; plans take a stream per msa_plan_execute. */
 int msa_set_stream(void *stream);
 
 /*

@@ -46,6 +46,7 @@ static cudaStream_t g_own_stream = nullptr;
 
 cudaStream_t library_stream(int *rc) {
     *rc = MSA_OK;
+    std::lock_guard<std::mutex> g(settings_mutex());  // msa_set_stream may run on another thread
     if (g_stream_set) return (cudaStream_t)g_stream;
     if (!g_own_stream) {
         cudaError_t e = cudaStreamCreateWithFlags(&g_own_stream, cudaStreamNonBlocking);
