@@ -303,6 +303,7 @@ def run_serving(n: int):
 def _oracle_warm(_: int) -> int:
     import oracle
     oracle.build()
+    time.sleep(0.2)  # keep this worker busy so that every worker gets a warm-up task
     return os.getpid()
 
 
@@ -313,17 +314,19 @@ def _oracle_serving_request(i: int) -> int:
     return p.cells
 
 
-def serving_cpu_baseline(n: int, procs: int = 0):
+def serving_cpu_baseline(n: int, procs: int = 0, timeout_s: float = 600.0):
     """The oracle on the first ``n`` requests of the serving stream, one request
     per task on ``procs`` spawned worker processes (default: every host core),
-    timed after the workers have started and loaded the oracle."""
+    timed after the workers have started and loaded the oracle. A worker that
+    dies raises instead of leaving the run waiting."""
     import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
     procs = procs or os.cpu_count() or 1
     ctx = mp.get_context("spawn")  # no fork of a process that holds a CUDA context
-    with ctx.Pool(procs) as pool:
-        pool.map(_oracle_warm, range(procs), chunksize=1)
+    with ProcessPoolExecutor(max_workers=procs, mp_context=ctx) as ex:
+        list(ex.map(_oracle_warm, range(procs), timeout=timeout_s))
         t0 = time.perf_counter()
-        cells = sum(pool.imap_unordered(_oracle_serving_request, range(n), chunksize=1))
+        cells = sum(ex.map(_oracle_serving_request, range(n), timeout=timeout_s))
         dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "alignments/s", "cores": procs, "kind": "oracle",
             "cells_per_s": cells / dt,

@@ -133,7 +133,10 @@ typedef struct msa_plan_info {
 typedef struct msa_device_result {
     int32_t score;   /* optimal SP score */
     int32_t ncols;   /* alignment columns */
-    int32_t status;  /* MSA_OK, MSA_EINVAL (bad residue / asymmetric table) or MSA_ETIMEOUT */
+    int32_t status;  /* MSA_OK; MSA_EINVAL (bad residue / asymmetric table), MSA_ETOOBIG (keys
+                        could leave the int32 range), MSA_ETIMEOUT (a dependency wait ran
+                        out), or another negative value if the traceback met an
+                        inconsistent tensor (reported as MSA_ECUDA by msa_align) */
     int32_t pad;
 } msa_device_result;
 
