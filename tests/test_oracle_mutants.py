@@ -23,6 +23,10 @@ MUTANTS = {
     "origin_not_zero": ("H[0] = 0;", "H[0] = 1;"),
     "columns_not_reversed": ("for (int32_t a = 0, b = ncols - 1; a < b; ++a, --b)",
                              "for (int32_t a = 0, b = ncols - 1; a < 0; ++a, --b)"),
+    "gap_gap_charged": ("} else if (in_i || in_j) {", "} else {"),
+    "full_move_skipped": ("for (int m = 1; m <= nmoves; ++m) {", "for (int m = 1; m < nmoves; ++m) {"),
+    "score_not_from_corner": ("*out_score = H[N - 1];", "*out_score = H[N > 1 ? N - 2 : 0];"),
+    "traceback_not_from_corner": ("int64_t l = N - 1;", "int64_t l = N > 1 ? N - 2 : 0;"),
 }
 
 
