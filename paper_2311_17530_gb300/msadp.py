@@ -214,7 +214,7 @@ class Plan:
         return np.lib.stride_tricks.as_strided(raw, shape=shape, strides=strides).copy()
 
     def timings(self) -> Tuple[float, float, float]:
-        """(encode, fill, traceback) milliseconds of the last timed execution."""
+        """Mean (encode, fill, traceback) milliseconds over the executions timed since the previous call."""
         out = (ctypes.c_float * 3)()
         _check(self._lib.msa_plan_timings(self._h, out))
         return float(out[0]), float(out[1]), float(out[2])
