@@ -57,3 +57,22 @@ def test_serving_cpu_baseline_runs_on_spawned_workers():
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["unit"] == "alignments/s"
     assert r["value"] > 0 and r["cells_per_s"] > 0
     assert "requests 0..2" in r["sample"]
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one JSON
+    line with the keys the benchmark contract asks of it."""
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "0", "--ref-cells", "2e5"], capture_output=True, text=True, timeout=300,
+                         cwd=ROOT, check=True).stdout
+    lines = [ln for ln in out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1
+    for key in ("metric", "value", "unit", "ms_per_step", "higher_is_better", "scaling", "dtype", "data", "config"):
+        assert key in d, key
+    assert d["config"]["workload"] == "k3_protein_700_760_800"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["value"] > 0
