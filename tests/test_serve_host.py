@@ -47,3 +47,44 @@ def test_unknown_handles_and_empty_queue():
     assert code_of(lambda: msa.msa_cancel(987654321)) == msa.MSA_EBADHANDLE
     assert msa.msa_wait_any(0) is None
     msa.msa_drain()  # nothing queued or running: returns at once
+
+
+def test_serving_without_a_device_fails_cleanly():
+    """With no usable GPU, serving fails cleanly: either msa_submit refuses the
+    request at once, or the loop's device set-up fails and the queued request
+    completes with that error (no hang); later submits are refused too. Runs in
+    its own process, since a failed loop stays failed for the process."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the serving loop would start")
+    code = r'''
+import sys
+sys.path.insert(0, %r)
+import inputs
+import paper_2311_17530_gb300 as msa
+dna = inputs.dna_table()
+try:
+    h = msa.msa_submit(["ACGT", "AGT"], inputs.DNA, dna, -8)
+except msa.MsaError as e:  # no device at all: refused before the loop starts
+    assert e.code == msa.MSA_ECUDA, e
+    h = None
+if h is not None:  # the loop started and its device set-up failed
+    got = msa.msa_wait_any(20 * 1000 * 1000)
+    assert got == h, (got, h)
+    try:
+        msa.msa_poll(h, 2, 7)
+        raise SystemExit("poll succeeded without a device")
+    except msa.MsaError as e:
+        assert e.code in (msa.MSA_ECUDA, msa.MSA_ENOMEM), e
+try:
+    msa.msa_submit(["ACGT", "AGT"], inputs.DNA, dna, -8)
+    raise SystemExit("submit accepted without a device")
+except msa.MsaError as e:
+    assert e.code in (msa.MSA_ECUDA, msa.MSA_ENOMEM), e
+assert msa.msa_wait_any(0) is None
+msa.msa_drain()
+print("ok")
+''' % ROOT
+    import sys
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", (out.stdout, out.stderr)
