@@ -9,7 +9,14 @@ Eq. 1 generalised to 2^k-1 neighbours; section 4 per-cell scoring; section 5.2
 sum-of-pairs columns with gap-gap 0; section 2 traceback). This wrapper only
 marshals arguments and expands the returned move masks into gapped rows.
 
-Every function here is pinned by ``tests/test_oracle_pins.py`` against brute
+``oracle_pair_tables`` / ``oracle_msa_pruned`` (``pair_tables``, ``align_pruned``)
+are the oracle of exact search-space pruning (section 6 proposes narrowing the
+search to the partitions where an optimal alignment can lie) by the
+Carrillo-Lipman bound: pairwise forward and backward tables and the same DP
+restricted to the cells whose bound reaches a lower bound on the optimum; they
+are pinned by ``tests/test_oracle_pruning.py``.
+
+``oracle_msa`` is pinned by ``tests/test_oracle_pins.py`` against brute
 force enumeration, textbook Needleman-Wunsch, a closed form, permutation
 invariance and the alignment invariants. The paper's own 6-sequence example
 (section 5.2, optimal SP score -5) is parity unpinned: its sequences are not
@@ -51,6 +58,15 @@ def load_library(path: str):
         ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int,
         ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
+    lib.oracle_pair_tables.restype = ctypes.c_int
+    lib.oracle_pair_tables.argtypes = [
+        ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int,
+        ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    lib.oracle_msa_pruned.restype = ctypes.c_int
+    lib.oracle_msa_pruned.argtypes = [
+        ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int,
+        ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+        ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
     return lib
 
 
@@ -124,3 +140,51 @@ def align(seqs: Sequence[str], alphabet: str, subst, gap: int, want_tb: bool = F
 
 def align_problem(p, want_tb: bool = False, want_H: bool = False) -> OracleResult:
     return align(p.seqs, p.alphabet, p.subst, p.gap, want_tb, want_H)
+
+
+# ---------------------------------------------------------------------------
+# Exact search-space pruning (Carrillo-Lipman bound; the paper's future work,
+# section 6): pairwise forward/backward tables and the DP over the cells whose
+# bound reaches a lower bound on the optimum.
+
+def pair_tables(a: str, b: str, alphabet: str, subst, gap: int, lib=None):
+    """(fwd, bwd): int64 arrays of shape (len(a)+1, len(b)+1); fwd[p, q] is the
+    optimal global score of a[:p] against b[:q], bwd[p, q] that of a[p:] against b[q:]."""
+    lib = lib or _load()
+    ca, cb = encode([a], alphabet), encode([b], alphabet)
+    sub = np.ascontiguousarray(np.asarray(subst, dtype=np.int32).reshape(-1))
+    fwd = np.empty((len(a) + 1, len(b) + 1), dtype=np.int64)
+    bwd = np.empty_like(fwd)
+    rc = lib.oracle_pair_tables(ca.ctypes.data if ca.size else None, len(a), cb.ctypes.data if cb.size else None,
+                                len(b), len(alphabet), sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(gap),
+                                fwd.ctypes.data, bwd.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_pair_tables failed with {rc}")
+    return fwd, bwd
+
+
+class BoundAboveOptimum(ValueError):
+    """The lower bound given to align_pruned exceeds the optimal score."""
+
+
+def align_pruned(seqs: Sequence[str], alphabet: str, subst, gap: int, lower_bound: int, lib=None):
+    """(OracleResult, cells left out): the DP restricted to cells whose
+    Carrillo-Lipman bound reaches ``lower_bound``. Raises BoundAboveOptimum when
+    no kept path reaches ``lower_bound``."""
+    lib = lib or _load()
+    k = len(seqs)
+    lens = [len(s) for s in seqs]
+    lens_arr = (ctypes.c_int32 * k)(*lens)
+    codes = encode(seqs, alphabet)
+    sub = np.ascontiguousarray(np.asarray(subst, dtype=np.int32).reshape(-1))
+    masks = np.zeros(max(1, sum(lens)), dtype=np.uint8)
+    score, ncols, excluded = ctypes.c_int64(0), ctypes.c_int32(0), ctypes.c_int64(0)
+    rc = lib.oracle_msa_pruned(k, lens_arr, codes.ctypes.data if codes.size else None, len(alphabet),
+                               sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(gap), int(lower_bound),
+                               ctypes.byref(score), masks.ctypes.data, ctypes.byref(ncols), ctypes.byref(excluded))
+    if rc == -3:
+        raise BoundAboveOptimum(f"no kept path reaches {lower_bound}")
+    if rc != 0:
+        raise ValueError(f"oracle_msa_pruned failed with {rc}")
+    ms = [int(m) for m in masks[: ncols.value]]
+    return OracleResult(int(score.value), ms, expand(seqs, ms), None, None), int(excluded.value)

@@ -172,3 +172,224 @@ int oracle_msa(int k, const int32_t *lens, const uint8_t *codes, int A,
     if (!out_tb) free(TB);
     return 0;
 }
+
+/*
+ * Exact search-space pruning, the restriction of the search space the paper
+ * leaves for future work (section 6), by the bound of Carrillo and Lipman: the
+ * score of an alignment is the sum over pairs of sequences of the scores of its
+ * pairwise projections (section 5.2 scores gap against gap 0, so dropping those
+ * columns leaves each projection's score unchanged), and a projection of an
+ * alignment through cell x is a pairwise alignment through (x_i, x_j).
+ *
+ * oracle_pair_tables: for residue codes a (na) and b (nb), two (na+1) x (nb+1)
+ * int64 arrays in row-major order,
+ *   fwd[p][q] = optimal global score of a[0:p] against b[0:q],
+ *   bwd[p][q] = optimal global score of a[p:na] against b[q:nb],
+ * by the pairwise recurrence (Eq. 1) with sub[x*A + y] for residue x of a
+ * against residue y of b and `gap` for a residue against a gap.
+ * Returns 0, or -1 on bad arguments.
+ */
+#define ORACLE_NEG (INT64_MIN / 4)
+
+int oracle_pair_tables(const uint8_t *a, int32_t na, const uint8_t *b, int32_t nb, int A,
+                       const int32_t *sub, int32_t gap, int64_t *fwd, int64_t *bwd)
+{
+    if (na < 0 || nb < 0 || A < 1 || !sub || !fwd || !bwd || (na > 0 && !a) || (nb > 0 && !b))
+        return -1;
+    for (int32_t p = 0; p < na; ++p)
+        if (a[p] >= A)
+            return -1;
+    for (int32_t q = 0; q < nb; ++q)
+        if (b[q] >= A)
+            return -1;
+    const int64_t W = (int64_t)nb + 1;
+    for (int64_t p = 0; p <= na; ++p) {
+        for (int64_t q = 0; q <= nb; ++q) {
+            if (p == 0 && q == 0) {
+                fwd[0] = 0;
+                continue;
+            }
+            int64_t best = ORACLE_NEG;
+            if (p > 0 && fwd[(p - 1) * W + q] + gap > best)
+                best = fwd[(p - 1) * W + q] + gap;
+            if (q > 0 && fwd[p * W + q - 1] + gap > best)
+                best = fwd[p * W + q - 1] + gap;
+            if (p > 0 && q > 0 && fwd[(p - 1) * W + q - 1] + sub[a[p - 1] * A + b[q - 1]] > best)
+                best = fwd[(p - 1) * W + q - 1] + sub[a[p - 1] * A + b[q - 1]];
+            fwd[p * W + q] = best;
+        }
+    }
+    for (int64_t p = na; p >= 0; --p) {
+        for (int64_t q = nb; q >= 0; --q) {
+            if (p == na && q == nb) {
+                bwd[p * W + q] = 0;
+                continue;
+            }
+            int64_t best = ORACLE_NEG;
+            if (p < na && bwd[(p + 1) * W + q] + gap > best)
+                best = bwd[(p + 1) * W + q] + gap;
+            if (q < nb && bwd[p * W + q + 1] + gap > best)
+                best = bwd[p * W + q + 1] + gap;
+            if (p < na && q < nb && bwd[(p + 1) * W + q + 1] + sub[a[p] * A + b[q]] > best)
+                best = bwd[(p + 1) * W + q + 1] + sub[a[p] * A + b[q]];
+            bwd[p * W + q] = best;
+        }
+    }
+    return 0;
+}
+
+/*
+ * oracle_msa restricted to the cells x whose bound
+ *   U(x) = sum_{i<j} fwd_ij[x_i][x_j] + bwd_ij[x_i][x_j]
+ * reaches lower_bound (any alignment through x scores at most U(x)). A cell left
+ * out is never a predecessor and never on the path. When lower_bound does not
+ * exceed the optimum, no cell of any optimal alignment is left out, and neither
+ * is any optimal predecessor of such a cell, so score and alignment equal
+ * oracle_msa's (same tie rule: masks ascending, strict >).
+ *
+ * out_excluded receives the number of cells left out by the bound.
+ * Returns 0; -1 bad arguments; -2 out of memory; -3 when no path of kept cells
+ * reaches the corner or the best one scores below lower_bound (the bound was
+ * above the optimum).
+ */
+int oracle_msa_pruned(int k, const int32_t *lens, const uint8_t *codes, int A,
+                      const int32_t *sub, int32_t gap, int64_t lower_bound,
+                      int64_t *out_score, uint8_t *out_masks, int32_t *out_ncols,
+                      int64_t *out_excluded)
+{
+    if (k < 2 || k > ORACLE_MAXK || !lens || !sub || A < 1 || !out_score ||
+        !out_masks || !out_ncols || !out_excluded)
+        return -1;
+    int64_t rho[ORACLE_MAXK], stride[ORACLE_MAXK];
+    const uint8_t *seq[ORACLE_MAXK];
+    int64_t total_len = 0;
+    for (int i = 0; i < k; ++i) {
+        if (lens[i] < 0)
+            return -1;
+        rho[i] = (int64_t)lens[i] + 1;
+        seq[i] = codes + total_len;
+        total_len += lens[i];
+    }
+    if (total_len > 0 && !codes)
+        return -1;
+    for (int64_t t = 0; t < total_len; ++t)
+        if (codes[t] >= A)
+            return -1;
+    int64_t N = 1;
+    for (int i = k - 1; i >= 0; --i) {
+        stride[i] = N;
+        N *= rho[i];
+    }
+
+    /* pairwise tables, pair (i, j) with i < j */
+    int64_t *fwd[ORACLE_MAXK][ORACLE_MAXK] = {{0}};
+    int64_t *bwd[ORACLE_MAXK][ORACLE_MAXK] = {{0}};
+    int rc = 0;
+    for (int i = 0; i < k && rc == 0; ++i)
+        for (int j = i + 1; j < k && rc == 0; ++j) {
+            size_t n = (size_t)(rho[i] * rho[j]);
+            fwd[i][j] = (int64_t *)malloc(n * sizeof(int64_t));
+            bwd[i][j] = (int64_t *)malloc(n * sizeof(int64_t));
+            if (!fwd[i][j] || !bwd[i][j])
+                rc = -2;
+            else
+                rc = oracle_pair_tables(seq[i], lens[i], seq[j], lens[j], A, sub, gap,
+                                        fwd[i][j], bwd[i][j]);
+        }
+    int64_t *H = rc ? NULL : (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    uint8_t *TB = rc ? NULL : (uint8_t *)malloc((size_t)N);
+    if (rc == 0 && (!H || !TB))
+        rc = -2;
+
+    const int nmoves = (1 << k) - 1;
+    int64_t excluded = 0;
+    int64_t x[ORACLE_MAXK];
+    for (int64_t l = 0; rc == 0 && l < N; ++l) {
+        int64_t rem = l;
+        for (int i = 0; i < k; ++i) {
+            x[i] = rem / stride[i];
+            rem -= x[i] * stride[i];
+        }
+        int64_t U = 0;
+        for (int i = 0; i < k; ++i)
+            for (int j = i + 1; j < k; ++j) {
+                int64_t idx = x[i] * rho[j] + x[j];
+                U += fwd[i][j][idx] + bwd[i][j][idx];
+            }
+        TB[l] = 0;
+        if (U < lower_bound) {
+            H[l] = ORACLE_NEG;
+            ++excluded;
+            continue;
+        }
+        if (l == 0) {
+            H[0] = 0;
+            continue;
+        }
+        int64_t best = ORACLE_NEG;
+        int best_m = 0;
+        for (int m = 1; m <= nmoves; ++m) {
+            int valid = 1;
+            int64_t pred = l;
+            for (int i = 0; i < k; ++i) {
+                if ((m >> i) & 1) {
+                    if (x[i] < 1) {
+                        valid = 0;
+                        break;
+                    }
+                    pred -= stride[i];
+                }
+            }
+            if (!valid || H[pred] == ORACLE_NEG)
+                continue;
+            int64_t sp = 0;
+            for (int i = 0; i < k; ++i) {
+                int in_i = (m >> i) & 1;
+                for (int j = i + 1; j < k; ++j) {
+                    int in_j = (m >> j) & 1;
+                    if (in_i && in_j)
+                        sp += sub[seq[i][x[i] - 1] * A + seq[j][x[j] - 1]];
+                    else if (in_i || in_j)
+                        sp += gap;
+                }
+            }
+            int64_t cand = H[pred] + sp;
+            if (best_m == 0 || cand > best) {
+                best = cand;
+                best_m = m;
+            }
+        }
+        H[l] = best_m ? best : ORACLE_NEG;
+        TB[l] = (uint8_t)best_m;
+    }
+
+    if (rc == 0 && (H[N - 1] == ORACLE_NEG || H[N - 1] < lower_bound))
+        rc = -3;
+    if (rc == 0) {
+        *out_score = H[N - 1];
+        *out_excluded = excluded;
+        int32_t ncols = 0;
+        int64_t l = N - 1;
+        while (l != 0) {
+            int m = TB[l];
+            out_masks[ncols++] = (uint8_t)m;
+            for (int i = 0; i < k; ++i)
+                if ((m >> i) & 1)
+                    l -= stride[i];
+        }
+        for (int32_t a = 0, b = ncols - 1; a < b; ++a, --b) {
+            uint8_t t = out_masks[a];
+            out_masks[a] = out_masks[b];
+            out_masks[b] = t;
+        }
+        *out_ncols = ncols;
+    }
+    free(H);
+    free(TB);
+    for (int i = 0; i < k; ++i)
+        for (int j = i + 1; j < k; ++j) {
+            free(fwd[i][j]);
+            free(bwd[i][j]);
+        }
+    return rc;
+}
