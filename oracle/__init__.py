@@ -14,7 +14,10 @@ are the oracle of exact search-space pruning (section 6 proposes narrowing the
 search to the partitions where an optimal alignment can lie) by the
 Carrillo-Lipman bound: pairwise forward and backward tables and the same DP
 restricted to the cells whose bound reaches a lower bound on the optimum; they
-are pinned by ``tests/test_oracle_pruning.py``.
+are pinned by ``tests/test_oracle_pruning.py``. ``oracle_msa_near_optimal``
+(``align_near_optimal``) enumerates every alignment within a threshold of the
+optimum (section 6: further optimal or near-optimal solutions), pinned by
+``tests/test_oracle_near_optimal.py``.
 
 ``oracle_msa`` is pinned by ``tests/test_oracle_pins.py`` against brute
 force enumeration, textbook Needleman-Wunsch, a closed form, permutation
@@ -67,6 +70,11 @@ def load_library(path: str):
         ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int,
         ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
+    lib.oracle_msa_near_optimal.restype = ctypes.c_int
+    lib.oracle_msa_near_optimal.argtypes = [
+        ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int,
+        ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
     return lib
 
 
@@ -188,3 +196,37 @@ def align_pruned(seqs: Sequence[str], alphabet: str, subst, gap: int, lower_boun
         raise ValueError(f"oracle_msa_pruned failed with {rc}")
     ms = [int(m) for m in masks[: ncols.value]]
     return OracleResult(int(score.value), ms, expand(seqs, ms), None, None), int(excluded.value)
+
+
+# ---------------------------------------------------------------------------
+# Optimal and near-optimal alignments (section 6: forking at equally ranked
+# paths, or within a user threshold).
+
+def align_near_optimal(seqs: Sequence[str], alphabet: str, subst, gap: int, delta: int = 0,
+                       max_count: int = 64, lib=None):
+    """(alignments, more): every alignment scoring at least OPT - ``delta``, in
+    increasing lexicographic order of the reversed column sequence (for
+    ``delta`` = 0 the first is ``align``'s), at most ``max_count`` of them; ``more`` is True when the
+    enumeration stopped at ``max_count``."""
+    lib = lib or _load()
+    k = len(seqs)
+    lens = [len(s) for s in seqs]
+    total = sum(lens)
+    lens_arr = (ctypes.c_int32 * k)(*lens)
+    codes = encode(seqs, alphabet)
+    sub = np.ascontiguousarray(np.asarray(subst, dtype=np.int32).reshape(-1))
+    masks = np.zeros((max_count, max(1, total)), dtype=np.uint8)
+    ncols = np.zeros(max_count, dtype=np.int32)
+    scores = np.zeros(max_count, dtype=np.int64)
+    count, more = ctypes.c_int32(0), ctypes.c_int32(0)
+    rc = lib.oracle_msa_near_optimal(k, lens_arr, codes.ctypes.data if codes.size else None, len(alphabet),
+                                     sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(gap), int(delta),
+                                     int(max_count), masks.ctypes.data, ncols.ctypes.data, scores.ctypes.data,
+                                     ctypes.byref(count), ctypes.byref(more))
+    if rc != 0:
+        raise ValueError(f"oracle_msa_near_optimal failed with {rc}")
+    out = []
+    for a in range(count.value):
+        ms = [int(m) for m in masks[a, : ncols[a]]]
+        out.append(OracleResult(int(scores[a]), ms, expand(seqs, ms), None, None))
+    return out, bool(more.value)

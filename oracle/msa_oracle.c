@@ -393,3 +393,143 @@ int oracle_msa_pruned(int k, const int32_t *lens, const uint8_t *codes, int A,
         }
     return rc;
 }
+
+/*
+ * Optimal and near-optimal alignments, the other extension the paper proposes
+ * (section 6: further solutions by forking at equally ranked paths, or within a
+ * user threshold). Every alignment scoring at least OPT - delta (delta >= 0;
+ * delta = 0: every optimal alignment), enumerated from the far corner with the
+ * moves of each column tried in increasing mask order, so alignments come in
+ * increasing lexicographic order of their reversed column sequence (for
+ * delta = 0 the first one is oracle_msa's). A move from x to its predecessor p is followed only
+ * when H(p) + SP(move) + (score of the columns already fixed) >= OPT - delta,
+ * H being the full forward tensor: H(p) is the best any completion through p
+ * can add, so no qualifying alignment is missed and none below the threshold is
+ * produced.
+ *
+ * Up to max_count alignments are stored: alignment a's masks (first column
+ * first) at out_masks + a * sum(lens), its column count in out_ncols[a], its
+ * score in out_scores[a]. *out_count receives the number stored, *out_more 1 when
+ * the enumeration stopped at max_count with more alignments left, else 0.
+ * Returns 0; -1 bad arguments; -2 out of memory.
+ */
+int oracle_msa_near_optimal(int k, const int32_t *lens, const uint8_t *codes, int A,
+                            const int32_t *sub, int32_t gap, int64_t delta, int32_t max_count,
+                            uint8_t *out_masks, int32_t *out_ncols, int64_t *out_scores,
+                            int32_t *out_count, int32_t *out_more)
+{
+    if (k < 1 || k > ORACLE_MAXK || !lens || !sub || A < 1 || delta < 0 || max_count < 1 ||
+        !out_masks || !out_ncols || !out_scores || !out_count || !out_more)
+        return -1;
+    int64_t rho[ORACLE_MAXK], stride[ORACLE_MAXK];
+    const uint8_t *seq[ORACLE_MAXK];
+    int64_t total_len = 0;
+    for (int i = 0; i < k; ++i) {
+        if (lens[i] < 0)
+            return -1;
+        rho[i] = (int64_t)lens[i] + 1;
+        seq[i] = codes + total_len;
+        total_len += lens[i];
+    }
+    if (total_len > 0 && !codes)
+        return -1;
+    int64_t N = 1;
+    for (int i = k - 1; i >= 0; --i) {
+        stride[i] = N;
+        N *= rho[i];
+    }
+    int64_t *H = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    uint8_t *tbuf = (uint8_t *)malloc((size_t)N);
+    uint8_t *path = (uint8_t *)malloc((size_t)total_len + 1);
+    int64_t *cell = (int64_t *)malloc(((size_t)total_len + 1) * sizeof(int64_t));
+    int64_t *acc = (int64_t *)malloc(((size_t)total_len + 1) * sizeof(int64_t));
+    int *next_m = (int *)malloc(((size_t)total_len + 1) * sizeof(int));
+    int rc = 0;
+    if (!H || !tbuf || !path || !cell || !acc || !next_m)
+        rc = -2;
+    int64_t score = 0;
+    int32_t nc = 0;
+    if (rc == 0)
+        rc = oracle_msa(k, lens, codes, A, sub, gap, &score, tbuf, H, path, &nc);
+    const int nmoves = (1 << k) - 1;
+    const int64_t threshold = score - delta;
+    int32_t count = 0;
+    *out_more = 0;
+    if (rc == 0) {
+        /* depth d: cell[d] reached after d columns fixed (from the corner), acc[d]
+           their score, next_m[d] the next move to try there */
+        int32_t d = 0;
+        cell[0] = N - 1;
+        acc[0] = 0;
+        next_m[0] = 1;
+        while (d >= 0) {
+            const int64_t l = cell[d];
+            if (l == 0) { /* reached the origin: an alignment */
+                if (count == max_count) {
+                    *out_more = 1;
+                    break;
+                }
+                uint8_t *dst = out_masks + (size_t)count * (size_t)total_len;
+                for (int32_t c = 0; c < d; ++c)
+                    dst[c] = path[d - 1 - c];
+                out_ncols[count] = d;
+                out_scores[count] = acc[d];
+                ++count;
+                --d;
+                continue;
+            }
+            int64_t x[ORACLE_MAXK];
+            int64_t rem = l;
+            for (int i = 0; i < k; ++i) {
+                x[i] = rem / stride[i];
+                rem -= x[i] * stride[i];
+            }
+            int advanced = 0;
+            while (next_m[d] <= nmoves) {
+                const int m = next_m[d]++;
+                int valid = 1;
+                int64_t pred = l;
+                for (int i = 0; i < k; ++i)
+                    if ((m >> i) & 1) {
+                        if (x[i] < 1) {
+                            valid = 0;
+                            break;
+                        }
+                        pred -= stride[i];
+                    }
+                if (!valid)
+                    continue;
+                int64_t sp = 0;
+                for (int i = 0; i < k; ++i) {
+                    int in_i = (m >> i) & 1;
+                    for (int j = i + 1; j < k; ++j) {
+                        int in_j = (m >> j) & 1;
+                        if (in_i && in_j)
+                            sp += sub[seq[i][x[i] - 1] * A + seq[j][x[j] - 1]];
+                        else if (in_i || in_j)
+                            sp += gap;
+                    }
+                }
+                if (H[pred] + sp + acc[d] >= threshold) {
+                    path[d] = (uint8_t)m;
+                    cell[d + 1] = pred;
+                    acc[d + 1] = acc[d] + sp;
+                    next_m[d + 1] = 1;
+                    ++d;
+                    advanced = 1;
+                    break;
+                }
+            }
+            if (!advanced)
+                --d;
+        }
+    }
+    *out_count = count;
+    free(H);
+    free(tbuf);
+    free(path);
+    free(cell);
+    free(acc);
+    free(next_m);
+    return rc;
+}
