@@ -99,6 +99,9 @@ int msa_set_stream(void *stream);
  *   "timing"            1: msa_plan_execute records per-stage CUDA events (default 0)
  *   "test_withhold_tile" test hook: the tile with this ticket never publishes its
  *                       completion, so its dependants time out (default -1: off)
+ *   "test_shuffle_waves" test hook: a nonzero seed makes later plans permute the
+ *                       tickets inside every wave (another topological order of
+ *                       the same tiles); 0 keeps the canonical order (default 0)
  */
 int msa_config(const char *key, int64_t value);
 

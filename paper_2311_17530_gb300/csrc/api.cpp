@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "api_internal.h"
+#include "plan_hooks.h"
 
 using namespace msadp;
 
@@ -288,6 +289,9 @@ int msa_config(const char *key, int64_t value) {
         s.timing = value ? 1 : 0;
     } else if (!strcmp(key, "test_withhold_tile")) {
         s.withhold = value;
+    } else if (!strcmp(key, "test_shuffle_waves")) {
+        if (value < 0) return set_error(MSA_EINVAL, "test_shuffle_waves must be >= 0");
+        set_wave_shuffle_seed((uint64_t)value);
     } else {
         return set_error(MSA_EINVAL, "unknown setting '%s'", key);
     }

@@ -4,8 +4,10 @@
 // fastest), the tile grid, and the ticket order of tiles by wave (section 3:
 // tiles whose coordinates sum to w form wave w and are mutually independent).
 #include "plan.h"
+#include "plan_hooks.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <mutex>
 
@@ -95,6 +97,32 @@ void wave_sizes(int k, const int32_t *grid, std::vector<int64_t> &out) {
 }
 
 static int64_t round_up64(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+static std::atomic<uint64_t> g_wave_shuffle_seed{0};
+void set_wave_shuffle_seed(uint64_t seed) { g_wave_shuffle_seed = seed; }
+uint64_t wave_shuffle_seed() { return g_wave_shuffle_seed; }
+
+// SplitMix64 (Steele, Lea and Flood's splittable generator, Vigna's constants).
+static uint64_t splitmix64(uint64_t &state) {
+    uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Test hook: permute the tickets inside every wave (Fisher-Yates, seeded). Every
+// producer of a tile lies in an earlier wave, so the order stays topological.
+static void shuffle_within_waves(HostPlan &hp) {
+    uint64_t state = wave_shuffle_seed();
+    if (state == 0) return;
+    for (size_t w = 0; w + 1 < hp.wave_start.size(); ++w) {
+        const int64_t b = hp.wave_start[w], e = hp.wave_start[w + 1];
+        for (int64_t i = e - 1; i > b; --i) {
+            const int64_t j = b + (int64_t)(splitmix64(state) % (uint64_t)(i - b + 1));
+            std::swap(hp.order[(size_t)i], hp.order[(size_t)j]);
+        }
+    }
+}
 
 bool score_and_traceback_layout(HostPlan &hp) {
     const int k = hp.k;
@@ -233,6 +261,7 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
         hp.wave_start.assign((size_t)(hp.G[0] + hp.G[1]), 0);
         for (int64_t t = 0; t < nt; ++t) hp.wave_start[(size_t)(t / hp.G[1] + t % hp.G[1] + 1)]++;
         for (size_t w = 1; w < hp.wave_start.size(); ++w) hp.wave_start[w] += hp.wave_start[w - 1];
+        shuffle_within_waves(hp);
         return MSA_OK;
     }
 
@@ -262,6 +291,7 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
     hp.wave_start = cnt;
     hp.order.assign(nt, 0);
     for (int64_t t = 0; t < nt; ++t) hp.order[cnt[wave_of[t]]++] = (uint64_t)t;
+    shuffle_within_waves(hp);
     return MSA_OK;
 }
 

@@ -2,16 +2,19 @@
 // for tile (and band) plans the order lists every tile once, by wave (sum of the
 // tile's grid coordinates, decoded here by division) and by increasing linear
 // index within a wave; for column plans by a + b; and wave_start marks where each
-// wave begins.
+// wave begins. With the wave-shuffle test hook on, the same holds except the
+// order inside a wave, which must differ from the canonical one somewhere.
 #include <cstdio>
 #include <string>
 #include <vector>
 
 #include "plan.h"
+#include "plan_hooks.h"
 
 using namespace msadp;
 
-static int check(int k, const int32_t *lens, int A, int kernel, int edge) {
+static int check(int k, const int32_t *lens, int A, int kernel, int edge, int64_t *moved = nullptr) {
+    const bool shuffled = wave_shuffle_seed() != 0;
     HostPlan hp;
     std::string err;
     if (make_plan(k, lens, A, kernel, hp, err, edge) != 0) return printf("plan failed: %s\n", err.c_str()), 1;
@@ -36,7 +39,8 @@ static int check(int k, const int32_t *lens, int A, int kernel, int edge) {
                     rem -= c * hp.gstride[i];
                     wave += c;
                 }
-                if (t <= prev) return printf("k=%d wave %zu not in index order\n", k, w), 1;
+                if (!shuffled && t <= prev) return printf("k=%d wave %zu not in index order\n", k, w), 1;
+                if (shuffled && moved && t <= prev) ++*moved;
             }
             if (wave != (int64_t)w) return printf("k=%d tile %lld in wave %zu, belongs to %lld\n", k, (long long)t, w, (long long)wave), 1;
             prev = t;
@@ -64,6 +68,17 @@ int main() {
     bad += check(6, l6, 4, 1, 3);
     bad += check(7, l7, 4, 1, 2);
     bad += check(8, l8, 4, 1, 2);
+    // another topological order: tickets permuted inside every wave
+    set_wave_shuffle_seed(12345);
+    int64_t moved = 0;
+    bad += check(2, l2, 20, 1, 32, &moved);
+    bad += check(3, l3, 20, 1, 12, &moved);
+    bad += check(3, l3c, 20, 2, -1);
+    bad += check(4, l4, 4, 1, 6, &moved);
+    bad += check(6, l6, 4, 1, 3, &moved);
+    bad += check(2, l2, 20, 3, -1);
+    if (moved == 0) bad += printf("shuffled plans kept the canonical order\n") > 0;
+    set_wave_shuffle_seed(0);
     if (!bad) printf("ok\n");
     return bad ? 1 : 0;
 }
