@@ -178,8 +178,8 @@ def k6_protein(seed: int = 4, table_seed: int = 2) -> Problem:
 def k2_protein(seed: int = 6, table_seed: int = 2) -> Problem:
     """k=2 protein pair, lengths 5000/4800 from one ancestor (sub 0.2, indel 0.05).
 
-    The pairwise case of the method (section 2, Eq. 1), sized so one problem
-    spans 157 bands of 32 rows. Uses the substitution table of :func:`k3_protein`.
+    The pairwise case of the method (section 2, Eq. 1), at 2.4e7 cells.
+    Uses the substitution table of :func:`k3_protein`.
     """
     table = protein_table(np.random.default_rng(table_seed))
     rng = np.random.default_rng(seed)
