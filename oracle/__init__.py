@@ -13,8 +13,11 @@ marshals arguments and expands the returned move masks into gapped rows.
 are the oracle of exact search-space pruning (section 6 proposes narrowing the
 search to the partitions where an optimal alignment can lie) by the
 Carrillo-Lipman bound: pairwise forward and backward tables and the same DP
-restricted to the cells whose bound reaches a lower bound on the optimum; they
-are pinned by ``tests/test_oracle_pruning.py``. ``oracle_msa_near_optimal``
+restricted to the cells whose bound reaches a lower bound on the optimum;
+``oracle_tile_bounds`` / ``oracle_msa_excluding`` (``tile_bounds``,
+``align_excluding``) the per-tile bound a fill that skips whole tiles uses and
+the DP with any set of cells left out; all pinned by
+``tests/test_oracle_pruning.py``. ``oracle_msa_near_optimal``
 (``align_near_optimal``) enumerates every alignment within a threshold of the
 optimum (section 6: further optimal or near-optimal solutions), pinned by
 ``tests/test_oracle_near_optimal.py``.
@@ -70,6 +73,15 @@ def load_library(path: str):
         ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int,
         ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
         ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)]
+    lib.oracle_tile_bounds.restype = ctypes.c_int
+    lib.oracle_tile_bounds.argtypes = [
+        ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int,
+        ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]
+    lib.oracle_msa_excluding.restype = ctypes.c_int
+    lib.oracle_msa_excluding.argtypes = [
+        ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int,
+        ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
+        ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)]
     lib.oracle_msa_near_optimal.restype = ctypes.c_int
     lib.oracle_msa_near_optimal.argtypes = [
         ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p, ctypes.c_int,
@@ -196,6 +208,49 @@ def align_pruned(seqs: Sequence[str], alphabet: str, subst, gap: int, lower_boun
         raise ValueError(f"oracle_msa_pruned failed with {rc}")
     ms = [int(m) for m in masks[: ncols.value]]
     return OracleResult(int(score.value), ms, expand(seqs, ms), None, None), int(excluded.value)
+
+
+
+def tile_bounds(seqs: Sequence[str], alphabet: str, subst, gap: int, extents: Sequence[int], lib=None) -> np.ndarray:
+    """Per-tile pruning bound (int64 array over the tile grid, tiles of ``extents``):
+    the sum over pairs of the largest pairwise forward + backward score in the tile's
+    rectangle, never below the largest cell bound inside the tile."""
+    lib = lib or _load()
+    k = len(seqs)
+    lens = [len(s) for s in seqs]
+    grid = tuple(-(-(n + 1) // int(e)) for n, e in zip(lens, extents))
+    out = np.empty(grid, dtype=np.int64)
+    codes = encode(seqs, alphabet)
+    sub = np.ascontiguousarray(np.asarray(subst, dtype=np.int32).reshape(-1))
+    rc = lib.oracle_tile_bounds(k, (ctypes.c_int32 * k)(*lens), codes.ctypes.data if codes.size else None,
+                                len(alphabet), sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(gap),
+                                (ctypes.c_int32 * k)(*[int(e) for e in extents]), out.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle_tile_bounds failed with {rc}")
+    return out
+
+
+def align_excluding(seqs: Sequence[str], alphabet: str, subst, gap: int, excluded: np.ndarray, lib=None):
+    """The DP with the cells flagged in ``excluded`` (bool array of shape len_i + 1)
+    left out; raises BoundAboveOptimum when no kept path reaches the corner."""
+    lib = lib or _load()
+    k = len(seqs)
+    lens = [len(s) for s in seqs]
+    ex = np.ascontiguousarray(np.asarray(excluded, dtype=np.uint8))
+    assert ex.shape == tuple(n + 1 for n in lens)
+    codes = encode(seqs, alphabet)
+    sub = np.ascontiguousarray(np.asarray(subst, dtype=np.int32).reshape(-1))
+    masks = np.zeros(max(1, sum(lens)), dtype=np.uint8)
+    score, ncols = ctypes.c_int64(0), ctypes.c_int32(0)
+    rc = lib.oracle_msa_excluding(k, (ctypes.c_int32 * k)(*lens), codes.ctypes.data if codes.size else None,
+                                  len(alphabet), sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(gap),
+                                  ex.ctypes.data, ctypes.byref(score), masks.ctypes.data, ctypes.byref(ncols))
+    if rc == -3:
+        raise BoundAboveOptimum("no kept path reaches the corner")
+    if rc != 0:
+        raise ValueError(f"oracle_msa_excluding failed with {rc}")
+    ms = [int(m) for m in masks[: ncols.value]]
+    return OracleResult(int(score.value), ms, expand(seqs, ms), None, None)
 
 
 # ---------------------------------------------------------------------------

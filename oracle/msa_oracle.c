@@ -533,3 +533,194 @@ int oracle_msa_near_optimal(int k, const int32_t *lens, const uint8_t *codes, in
     free(next_m);
     return rc;
 }
+
+/*
+ * Per-tile bound for pruning whole partitions (section 6 proposes searching only
+ * the partitions where an optimal alignment can lie). Tiles have extents E[i]
+ * per axis (tile grid G_i = ceil((len_i + 1) / E_i), tiles numbered row-major,
+ * last axis fastest); out_bound[t] = sum over pairs i < j of the largest
+ * fwd_ij + bwd_ij over the tile's range of axis i times its range of axis j.
+ * A sum of maxima, so never below the largest cell bound U(x) inside the tile:
+ * a tile whose bound is below a lower bound on the optimum holds no cell of any
+ * optimal alignment. out_bound needs prod G_i entries.
+ * Returns 0; -1 bad arguments; -2 out of memory.
+ */
+int oracle_tile_bounds(int k, const int32_t *lens, const uint8_t *codes, int A,
+                       const int32_t *sub, int32_t gap, const int32_t *E, int64_t *out_bound)
+{
+    if (k < 2 || k > ORACLE_MAXK || !lens || !sub || A < 1 || !E || !out_bound)
+        return -1;
+    int64_t rho[ORACLE_MAXK], G[ORACLE_MAXK], gstride[ORACLE_MAXK];
+    const uint8_t *seq[ORACLE_MAXK];
+    int64_t total_len = 0;
+    for (int i = 0; i < k; ++i) {
+        if (lens[i] < 0 || E[i] < 1)
+            return -1;
+        rho[i] = (int64_t)lens[i] + 1;
+        G[i] = (rho[i] + E[i] - 1) / E[i];
+        seq[i] = codes + total_len;
+        total_len += lens[i];
+    }
+    if (total_len > 0 && !codes)
+        return -1;
+    int64_t NT = 1;
+    for (int i = k - 1; i >= 0; --i) {
+        gstride[i] = NT;
+        NT *= G[i];
+    }
+    for (int64_t t = 0; t < NT; ++t)
+        out_bound[t] = 0;
+    int rc = 0;
+    for (int i = 0; i < k && rc == 0; ++i)
+        for (int j = i + 1; j < k && rc == 0; ++j) {
+            size_t n = (size_t)(rho[i] * rho[j]);
+            int64_t *fwd = (int64_t *)malloc(n * sizeof(int64_t));
+            int64_t *bwd = (int64_t *)malloc(n * sizeof(int64_t));
+            int64_t *blk = (int64_t *)malloc((size_t)(G[i] * G[j]) * sizeof(int64_t));
+            if (!fwd || !bwd || !blk)
+                rc = -2;
+            else
+                rc = oracle_pair_tables(seq[i], lens[i], seq[j], lens[j], A, sub, gap, fwd, bwd);
+            if (rc == 0) {
+                /* largest fwd + bwd over each block of the (i, j) plane */
+                for (int64_t b = 0; b < G[i] * G[j]; ++b)
+                    blk[b] = ORACLE_NEG;
+                for (int64_t p = 0; p < rho[i]; ++p)
+                    for (int64_t q = 0; q < rho[j]; ++q) {
+                        int64_t v = fwd[p * rho[j] + q] + bwd[p * rho[j] + q];
+                        int64_t b = (p / E[i]) * G[j] + q / E[j];
+                        if (v > blk[b])
+                            blk[b] = v;
+                    }
+                for (int64_t t = 0; t < NT; ++t) {
+                    int64_t ci = (t / gstride[i]) % G[i], cj = (t / gstride[j]) % G[j];
+                    out_bound[t] += blk[ci * G[j] + cj];
+                }
+            }
+            free(fwd);
+            free(bwd);
+            free(blk);
+        }
+    return rc;
+}
+
+/*
+ * oracle_msa with the cells flagged in `excluded` (N bytes, row-major, nonzero:
+ * left out) never used: not computed, never a predecessor, never on the path.
+ * For parity of a fill that skips tiles: when every flagged cell has a bound
+ * below a lower bound on the optimum, score and alignment equal oracle_msa's.
+ * Returns 0; -1 bad arguments; -2 out of memory; -3 when no path of kept cells
+ * reaches the corner.
+ */
+int oracle_msa_excluding(int k, const int32_t *lens, const uint8_t *codes, int A,
+                         const int32_t *sub, int32_t gap, const uint8_t *excluded,
+                         int64_t *out_score, uint8_t *out_masks, int32_t *out_ncols)
+{
+    if (k < 1 || k > ORACLE_MAXK || !lens || !sub || A < 1 || !excluded || !out_score ||
+        !out_masks || !out_ncols)
+        return -1;
+    int64_t rho[ORACLE_MAXK], stride[ORACLE_MAXK];
+    const uint8_t *seq[ORACLE_MAXK];
+    int64_t total_len = 0;
+    for (int i = 0; i < k; ++i) {
+        if (lens[i] < 0)
+            return -1;
+        rho[i] = (int64_t)lens[i] + 1;
+        seq[i] = codes + total_len;
+        total_len += lens[i];
+    }
+    if (total_len > 0 && !codes)
+        return -1;
+    for (int64_t t = 0; t < total_len; ++t)
+        if (codes[t] >= A)
+            return -1;
+    int64_t N = 1;
+    for (int i = k - 1; i >= 0; --i) {
+        stride[i] = N;
+        N *= rho[i];
+    }
+    int64_t *H = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    uint8_t *TB = (uint8_t *)malloc((size_t)N);
+    if (!H || !TB) {
+        free(H);
+        free(TB);
+        return -2;
+    }
+    const int nmoves = (1 << k) - 1;
+    int64_t x[ORACLE_MAXK];
+    for (int64_t l = 0; l < N; ++l) {
+        int64_t rem = l;
+        for (int i = 0; i < k; ++i) {
+            x[i] = rem / stride[i];
+            rem -= x[i] * stride[i];
+        }
+        TB[l] = 0;
+        if (excluded[l]) {
+            H[l] = ORACLE_NEG;
+            continue;
+        }
+        if (l == 0) {
+            H[0] = 0;
+            continue;
+        }
+        int64_t best = ORACLE_NEG;
+        int best_m = 0;
+        for (int m = 1; m <= nmoves; ++m) {
+            int valid = 1;
+            int64_t pred = l;
+            for (int i = 0; i < k; ++i) {
+                if ((m >> i) & 1) {
+                    if (x[i] < 1) {
+                        valid = 0;
+                        break;
+                    }
+                    pred -= stride[i];
+                }
+            }
+            if (!valid || H[pred] == ORACLE_NEG)
+                continue;
+            int64_t sp = 0;
+            for (int i = 0; i < k; ++i) {
+                int in_i = (m >> i) & 1;
+                for (int j = i + 1; j < k; ++j) {
+                    int in_j = (m >> j) & 1;
+                    if (in_i && in_j)
+                        sp += sub[seq[i][x[i] - 1] * A + seq[j][x[j] - 1]];
+                    else if (in_i || in_j)
+                        sp += gap;
+                }
+            }
+            int64_t cand = H[pred] + sp;
+            if (best_m == 0 || cand > best) {
+                best = cand;
+                best_m = m;
+            }
+        }
+        H[l] = best_m ? best : ORACLE_NEG;
+        TB[l] = (uint8_t)best_m;
+    }
+    int rc = 0;
+    if (H[N - 1] == ORACLE_NEG) {
+        rc = -3;
+    } else {
+        *out_score = H[N - 1];
+        int32_t ncols = 0;
+        int64_t l = N - 1;
+        while (l != 0) {
+            int m = TB[l];
+            out_masks[ncols++] = (uint8_t)m;
+            for (int i = 0; i < k; ++i)
+                if ((m >> i) & 1)
+                    l -= stride[i];
+        }
+        for (int32_t a = 0, b = ncols - 1; a < b; ++a, --b) {
+            uint8_t t = out_masks[a];
+            out_masks[a] = out_masks[b];
+            out_masks[b] = t;
+        }
+        *out_ncols = ncols;
+    }
+    free(H);
+    free(TB);
+    return rc;
+}

@@ -186,3 +186,116 @@ def test_planted_pruning_mistake_is_caught(name, tmp_path):
     lib = oracle.load_library(str(so))
     with pytest.raises((AssertionError, oracle.BoundAboveOptimum)):
         _pruning_pins(lib)
+
+
+# --- whole tiles: the per-tile bound and the DP with cells left out -------------
+
+def _expand_tiles(mask, extents, shape):
+    out = mask
+    for ax, e in enumerate(extents):
+        out = np.repeat(out, e, axis=ax)
+    return out[tuple(slice(0, n) for n in shape)]
+
+
+def test_tile_bound_is_never_below_the_cells_inside():
+    rng = np.random.default_rng(45)
+    for lens, ext in [((4, 5, 3), (2, 2, 2)), ((5, 3, 4), (3, 2, 4)), ((6, 7), (3, 2)), ((3, 3, 2, 3), (2, 2, 2, 2))]:
+        seqs = [inputs.random_seq(rng, "ACG", n) for n in lens]
+        table, gap = _asym(13 + sum(lens), 3), -2
+        U = _pair_bound(seqs, "ACG", table, gap)
+        tb = oracle.tile_bounds(seqs, "ACG", table, gap, ext)
+        for t in itertools.product(*[range(g) for g in tb.shape]):
+            cells = U[tuple(slice(c * e, (c + 1) * e) for c, e in zip(t, ext))]
+            assert tb[t] >= cells.max(), (lens, ext, t)
+            if len(lens) == 2:  # one pair: the bound is the tile's largest cell bound
+                assert tb[t] == cells.max()
+
+
+def test_skipping_tiles_below_the_bound_keeps_the_result():
+    for k, lens, ext in [(3, [30, 28, 33], (8, 8, 8)), (4, [9, 10, 8, 11], (3, 3, 3, 3)), (2, [60, 55], (16, 16))]:
+        p = inputs.random_problem(60 + k, k, lens, alphabet=inputs.PROTEIN, related=True)
+        full = oracle.align_problem(p)
+        shape = tuple(n + 1 for n in lens)
+        for L in (full.score, full.score - 4):
+            skip = oracle.tile_bounds(p.seqs, p.alphabet, p.subst, p.gap, ext) < L
+            assert skip.any()
+            r = oracle.align_excluding(p.seqs, p.alphabet, p.subst, p.gap, _expand_tiles(skip, ext, shape))
+            assert (r.score, r.masks) == (full.score, full.masks), (p.name, L)
+
+
+def test_any_subset_of_prunable_cells_keeps_the_result():
+    rng = np.random.default_rng(46)
+    for lens in [(4, 5, 4), (6, 5)]:
+        seqs = [inputs.random_seq(rng, "ACG", n) for n in lens]
+        table, gap = _asym(17 + sum(lens), 3), -2
+        U = _pair_bound(seqs, "ACG", table, gap)
+        full = oracle.align(seqs, "ACG", table, gap)
+        plain = oracle.align_excluding(seqs, "ACG", table, gap, np.zeros(U.shape, dtype=bool))
+        assert (plain.score, plain.masks) == (full.score, full.masks)
+        for rep in range(5):
+            ex = (U < full.score - rep) & (rng.random(U.shape) < 0.6)
+            r = oracle.align_excluding(seqs, "ACG", table, gap, ex)
+            assert (r.score, r.masks) == (full.score, full.masks)
+
+
+def test_leaving_out_a_cell_of_the_optimal_path_changes_the_path():
+    p = inputs.random_problem(9, 3, [12, 11, 13], related=True)
+    full = oracle.align_problem(p)
+    x = [0, 0, 0]
+    for m in full.masks[: len(full.masks) // 2]:  # walk half of the path from the origin
+        x = [x[i] + ((m >> i) & 1) for i in range(3)]
+    ex = np.zeros(tuple(n + 1 for n in p.lens), dtype=bool)
+    ex[tuple(x)] = True
+    try:
+        r = oracle.align_excluding(p.seqs, p.alphabet, p.subst, p.gap, ex)
+        assert r.masks != full.masks and r.score <= full.score
+    except oracle.BoundAboveOptimum:
+        pass
+
+
+TILE_MUTANTS = {
+    "tile_bound_keeps_last_pair_only": ("out_bound[t] += blk[ci * G[j] + cj];", "out_bound[t] = blk[ci * G[j] + cj];"),
+    "tile_bound_takes_minimum": ("if (v > blk[b])", "if (blk[b] == ORACLE_NEG || v < blk[b])"),
+    "exclusions_ignored": ("if (excluded[l]) {", "if (0) {"),
+}
+
+
+def _tile_pins(lib):
+    rng = np.random.default_rng(47)
+    seqs = [inputs.random_seq(rng, "ACG", n) for n in (5, 3, 4)]
+    table, gap = _asym(19, 3), -2
+    U = _pair_bound(seqs, "ACG", table, gap)
+    tb = oracle.tile_bounds(seqs, "ACG", table, gap, (2, 2, 2), lib=lib)
+    for t in itertools.product(*[range(g) for g in tb.shape]):
+        assert tb[t] >= U[tuple(slice(2 * c, 2 * c + 2) for c in t)].max()
+    full = oracle.align(seqs, "ACG", table, gap)
+    x = [0, 0, 0]
+    for m in full.masks[:3]:
+        x = [x[i] + ((m >> i) & 1) for i in range(3)]
+    ex = np.zeros(U.shape, dtype=bool)
+    ex[tuple(x)] = True
+    try:
+        r = oracle.align_excluding(seqs, "ACG", table, gap, ex, lib=lib)
+        assert r.masks != full.masks
+    except oracle.BoundAboveOptimum:
+        pass
+
+
+def test_unmutated_tile_pruning_passes_the_battery():
+    _tile_pins(None)
+
+
+@pytest.mark.parametrize("name", sorted(TILE_MUTANTS))
+def test_planted_tile_pruning_mistake_is_caught(name, tmp_path):
+    old, new = TILE_MUTANTS[name]
+    src = open(SRC).read()
+    marker = "int oracle_tile_bounds("
+    head, tail = src.split(marker, 1)
+    assert tail.count(old) == 1, f"mutation anchor for {name} not unique"
+    cpath = tmp_path / "mutant.c"
+    cpath.write_text(head + marker + tail.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", str(so), str(cpath)])
+    lib = oracle.load_library(str(so))
+    with pytest.raises(AssertionError):
+        _tile_pins(lib)
