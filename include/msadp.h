@@ -95,10 +95,13 @@ int msa_set_stream(void *stream);
  *   "batching"          1: serve by continuous batching; 0: one plain launch per
  *                       request, in arrival order (default 1)
  *   "fill_kernel"       0: automatic; 1: generic tile kernel; 2: k=3 column kernel;
- *                       3: k=2 band kernel
+ *                       3: k=2 band kernel; 4: k=4..6 line kernel
  *   "timing"            1: msa_plan_execute records per-stage CUDA events (default 0)
  *   "test_withhold_tile" test hook: the tile with this ticket never publishes its
  *                       completion, so its dependants time out (default -1: off)
+ *   "test_poison_tb"    test hook: 1 makes msa_plan_execute fill the plan's traceback
+ *                       tensor with 0xFF before the fill, so a cell the fill never
+ *                       writes keeps a value no move has for k < 8 (default 0)
  *   "test_shuffle_waves" test hook: a nonzero seed makes later plans permute the
  *                       tickets inside every wave (another topological order of
  *                       the same tiles); 0 keeps the canonical order (default 0)
@@ -124,12 +127,13 @@ typedef struct msa_plan_info {
     int32_t tile_extent[MSA_MAX_K];
     int64_t tiles;
     int32_t waves;              /* tile hyperplanes (section 3.1, Eq. 2) */
-    int32_t fill_kernel;        /* 1 generic tile kernel, 2 k=3 column kernel, 3 k=2 band kernel */
+    int32_t fill_kernel;        /* 1 generic tile kernel, 2 k=3 column kernel, 3 k=2 band kernel,
+                                   4 k=4..6 line kernel */
     void   *d_tb;               /* device pointer of the uint8 traceback tensor: row-major with
                                    tb_strides for the tile kernel (k <= 3) and the band kernel;
-                                   tile-major for the tile kernel at k >= 4; for the k=3 column
-                                   kernel a column-blocked layout (msa_plan_read_tb returns
-                                   row-major) */
+                                   tile-major for the tile kernel at k >= 4 and for the line
+                                   kernel; for the k=3 column kernel a column-blocked layout
+                                   (msa_plan_read_tb returns row-major) */
 } msa_plan_info;
 
 /* Result block written on the device by msa_plan_execute. */
@@ -283,6 +287,17 @@ int msa_tile_shape(int k, const int32_t *lens, int32_t *out_extent, int32_t *out
 int msa_set_tile_edge(int k, int32_t edge);
 int msa_get_tile_edge(int k, int32_t *out_edge);
 
+/*
+ * Longest segment of the last axis that one tile of the line kernel (k = 4..6)
+ * sweeps; the planner cuts the axis into equal segments no longer than this.
+ * Only compiled lengths are accepted (k=4: 32 64; k=5: 16 32; k=6: 16 25); 0
+ * restores the default (32, 32, 25) and the automatic choice of the line kernel
+ * for k = 4..6. Later plans and serving batches use the setting. Host-only,
+ * thread-safe; MSA_EINVAL for other k or lengths.
+ */
+int msa_set_line_segment(int k, int32_t z);
+int msa_get_line_segment(int k, int32_t *out_z);
+
 /* ------------------------------------------------------------------------ */
 /* Autotuner (no counterpart in the paper, which fixes S by hand).          */
 /* ------------------------------------------------------------------------ */
@@ -292,19 +307,21 @@ int msa_get_tile_edge(int k, int32_t *out_edge);
 typedef struct msa_tuning {
     int32_t k;
     int32_t ncand;                                   /* candidates timed */
-    int32_t cand_kernel[MSA_MAX_TUNING_CANDIDATES];  /* 1 generic tiles, 2 k=3 column, 3 k=2 band */
-    int32_t cand_edge[MSA_MAX_TUNING_CANDIDATES];    /* tile edge (0 for the column and band kernels) */
+    int32_t cand_kernel[MSA_MAX_TUNING_CANDIDATES];  /* 1 generic tiles, 2 k=3 column, 3 k=2 band, 4 lines */
+    int32_t cand_edge[MSA_MAX_TUNING_CANDIDATES];    /* tile edge; line segment for the line kernel;
+                                                        0 for the column and band kernels */
     float cand_ms[MSA_MAX_TUNING_CANDIDATES];        /* mean ms of one execution (encode+fill+traceback) */
     int32_t best;                                    /* index of the chosen candidate */
 } msa_tuning;
 
 /*
  * Time every compiled tile edge for k (and the column kernel for k = 3, the band
- * kernel for k = 2) on a synthetic problem with these lengths over an alphabet of
- * alphabet_size letters: one warm-up and `repeats` executions each, on the
- * library stream. The fastest becomes the choice for k (msa_set_tile_edge, and
- * for k = 2, 3 whether the automatic kernel choice takes the band or column
- * kernel). Allocates device memory; synchronous.
+ * kernel for k = 2, each compiled line segment for k = 4..6) on a synthetic
+ * problem with these lengths over an alphabet of alphabet_size letters: one
+ * warm-up and `repeats` executions each, on the library stream. The fastest
+ * becomes the choice for k (msa_set_tile_edge or msa_set_line_segment, and
+ * whether the automatic kernel choice takes the band, column or line kernel).
+ * Allocates device memory; synchronous.
  */
 int msa_autotune(int k, const int32_t *lens, int alphabet_size, int32_t repeats, msa_tuning *out);
 

@@ -119,22 +119,27 @@ int device_sm_count() {
 int persistent_grid(int k, int kernel, int64_t units, int A, int edge) {
     // resident CTAs per SM, cached per (kernel, k, alphabet size or tile edge)
     static std::mutex mu;
-    static int cache[4][MSA_MAX_K + 1][MSA_MAX_ALPHABET + 1] = {};
+    static int cache[5][MSA_MAX_K + 1][MSA_MAX_ALPHABET + 1] = {};
     int c;
     {
         std::lock_guard<std::mutex> g(mu);
-        int &slot = cache[kernel][k][kernel == kKernelCol3 ? A : (edge & 31)];
+        const int sub = kernel == kKernelCol3    ? A
+                      : kernel == kKernelLines ? (edge == line_z_candidate(k, 0) ? 1 : 2)
+                                               : (edge & 31);
+        int &slot = cache[kernel][k][sub];
         if (!slot) {
             slot = kernel == kKernelCol3    ? fill_col3_ctas_per_sm(col3_smem_bytes(A))
                    : kernel == kKernelBand2 ? fill_band2_ctas_per_sm()
+                   : kernel == kKernelLines ? fill_lines_ctas_per_sm(k, edge)
                                             : fill_tiles_ctas_per_sm(k, edge);
             if (slot <= 0) slot = 1;
         }
         c = slot;
     }
-    // the tile and band kernels take one unit per warp, the column kernel one per CTA
+    // the tile, line and band kernels take one unit per warp, the column kernel one per CTA
     const int per_cta = kernel == kKernelCol3    ? 1
                       : kernel == kKernelBand2 ? fill_band2_warps_per_cta()
+                      : kernel == kKernelLines ? std::max(1, fill_lines_warps_per_cta(k, edge))
                                                : std::max(1, fill_tiles_warps_per_cta(k, edge));
     int64_t need = (units + per_cta - 1) / per_cta;
     int64_t g = (int64_t)c * device_sm_count();
@@ -198,10 +203,13 @@ void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_
         d.gstride[i] = hp.gstride[i];
         d.qstride[i] = hp.qstride[i];
         d.tbstride[i] = hp.tbstride[i];
+        d.lst[i] = hp.lst[i];
     }
+    d.tb_block = hp.tb_block;
+    d.lzq = hp.lzq;
     d.tile_base = tile_base;
     d.ntiles = hp.ntiles;
-    d.has_qcorner = hp.kernel == kKernelTiles ? 1 : 0;
+    d.has_qcorner = hp.kernel == kKernelTiles || hp.kernel == kKernelLines ? 1 : 0;
     d.face0_stride = hp.face0_stride;
     d.face1_stride = hp.face1_stride;
     d.face0_rows = hp.face0_rows;
@@ -230,6 +238,7 @@ cudaError_t clear_faces(const HostPlan &hp, const PlanPointers &pp, cudaStream_t
 int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t s) {
     cudaError_t e = hp.kernel == kKernelCol3    ? launch_fill_col3(L, grid, col3_smem_bytes(hp.A), s)
                   : hp.kernel == kKernelBand2 ? launch_fill_band2(L, grid, s)
+                  : hp.kernel == kKernelLines ? launch_fill_lines(hp.k, hp.edge, L, grid, s)
                                               : launch_fill_tiles(hp.k, hp.edge, L, grid, s);
     return e == cudaSuccess ? MSA_OK : cuda_error(e, "fill kernel launch");
 }
@@ -283,12 +292,14 @@ int msa_config(const char *key, int64_t value) {
     } else if (!strcmp(key, "batching")) {
         s.batching = value ? 1 : 0;
     } else if (!strcmp(key, "fill_kernel")) {
-        if (value < 0 || value > 3) return set_error(MSA_EINVAL, "fill_kernel must be 0, 1, 2 or 3");
+        if (value < 0 || value > 4) return set_error(MSA_EINVAL, "fill_kernel must be 0, 1, 2, 3 or 4");
         s.fill_kernel = value;
     } else if (!strcmp(key, "timing")) {
         s.timing = value ? 1 : 0;
     } else if (!strcmp(key, "test_withhold_tile")) {
         s.withhold = value;
+    } else if (!strcmp(key, "test_poison_tb")) {
+        s.poison_tb = value ? 1 : 0;
     } else if (!strcmp(key, "test_shuffle_waves")) {
         if (value < 0) return set_error(MSA_EINVAL, "test_shuffle_waves must be >= 0");
         set_wave_shuffle_seed((uint64_t)value);
@@ -365,12 +376,13 @@ int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_su
     if (!plan || !d_subst || !d_result || (plan->hp.len_sum > 0 && (!d_residues || !d_masks)))
         return set_error(MSA_EINVAL, "NULL plan or device pointer");
     cudaStream_t s = (cudaStream_t)stream;
-    int64_t spin_ms, withhold, timing;
+    int64_t spin_ms, withhold, timing, poison;
     {
         std::lock_guard<std::mutex> g(settings_mutex());
         spin_ms = settings().spin_ms;
         withhold = settings().withhold;
         timing = settings().timing;
+        poison = settings().poison_tb;
     }
     plan->last_stream = s;
     cudaEvent_t *ev = nullptr;
@@ -384,6 +396,7 @@ int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_su
         cudaEventRecord(ev[0], s);
     }
     cudaError_t e = cudaMemsetAsync(plan->ws, 0, plan->reset_bytes, s);
+    if (e == cudaSuccess && poison) e = cudaMemsetAsync(plan->pp.tb, 0xFF, (size_t)plan->hp.tb_dev_bytes, s);
     if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
     IODesc io{d_residues, d_subst, d_result, d_masks, gap, 0};
     e = launch_encode(plan->pp.prob, 1, plan->hp.len_sum, nullptr, io, s);
@@ -457,11 +470,10 @@ int msa_plan_read_tb(msa_plan *plan, void *host_dst, int64_t bytes) {
     e = cudaMemcpy(dev.data(), plan->pp.tb, dev.size(), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "traceback tensor copy");
     uint8_t *out = static_cast<uint8_t *>(host_dst);
-    if (hp.tb_layout == 2) {
-        // tile-major device layout -> row-major host copy, cell by cell
+    if (hp.tb_layout == 2 || hp.tb_layout == 3) {
+        // tile-major device layouts -> row-major host copy, cell by cell: tile t's
+        // block of tb_block bytes, the cell at sum_i (local coordinate i) * lst[i]
         const int k = hp.k;
-        int64_t vol = 1;
-        for (int i = 0; i < k; ++i) vol *= hp.E[i];
         int x[MSA_MAX_K] = {};
         for (int64_t n = 0; n < hp.cells; ++n) {
             int64_t dst = 0, t = 0, loc = 0;
@@ -469,9 +481,9 @@ int msa_plan_read_tb(msa_plan *plan, void *host_dst, int64_t bytes) {
                 dst += x[i] * hp.tbstride[i];
                 const int q = x[i] / hp.E[i];
                 t += q * hp.gstride[i];
-                loc = loc * hp.E[i] + (x[i] - q * hp.E[i]);
+                loc += (int64_t)(x[i] - q * hp.E[i]) * hp.lst[i];
             }
-            if (dst < bytes) out[dst] = dev[(size_t)(t * vol + loc)];
+            if (dst < bytes) out[dst] = dev[(size_t)(t * hp.tb_block + loc)];
             for (int i = k - 1; i >= 0; --i) {  // next cell in row-major order
                 if (++x[i] < hp.rho[i]) break;
                 x[i] = 0;

@@ -1,5 +1,5 @@
-// Encode + table kernel (hot-path step a1) and the single-warp traceback kernel
-// (step a4), plus the per-k dispatch of the generic tile fill.
+// Encode + table kernel (hot-path step a1), plus the per-k dispatch of the
+// generic tile fill and of the line-sweep fill.
 #include "device_common.cuh"
 
 namespace msadp {
@@ -123,6 +123,42 @@ int fill_tiles_warps_per_cta(int k, int edge) {
     }
 }
 
+#define MSADP_LINES_K(k)                                                                      \
+    cudaError_t launch_fill_lines_k##k(int z, const LaunchDesc &L, int grid, cudaStream_t s); \
+    int fill_lines_ctas_k##k(int z);                                                          \
+    int fill_lines_warps_k##k(int z);
+MSADP_LINES_K(4)
+MSADP_LINES_K(5)
+MSADP_LINES_K(6)
+#undef MSADP_LINES_K
+
+cudaError_t launch_fill_lines(int k, int z, const LaunchDesc &L, int grid, cudaStream_t s) {
+    switch (k) {
+        case 4: return launch_fill_lines_k4(z, L, grid, s);
+        case 5: return launch_fill_lines_k5(z, L, grid, s);
+        case 6: return launch_fill_lines_k6(z, L, grid, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int fill_lines_ctas_per_sm(int k, int z) {
+    switch (k) {
+        case 4: return fill_lines_ctas_k4(z);
+        case 5: return fill_lines_ctas_k5(z);
+        case 6: return fill_lines_ctas_k6(z);
+        default: return 0;
+    }
+}
+
+int fill_lines_warps_per_cta(int k, int z) {
+    switch (k) {
+        case 4: return fill_lines_warps_k4(z);
+        case 5: return fill_lines_warps_k5(z);
+        case 6: return fill_lines_warps_k6(z);
+        default: return 0;
+    }
+}
+
 cudaError_t col3_attributes();
 
 // Every kernel attribute the launch wrappers need on the current device, so that
@@ -133,6 +169,10 @@ cudaError_t prepare_kernel_attributes() {
     for (int k = 2; k <= MSA_MAX_K && e == cudaSuccess; ++k)
         for (int i = 0; i < kMaxTileEdges && e == cudaSuccess; ++i)
             if (tile_edge_candidate(k, i) > 0 && fill_tiles_ctas_per_sm(k, tile_edge_candidate(k, i)) <= 0)
+                e = cudaErrorInvalidValue;
+    for (int k = kLinesMinK; k <= kLinesMaxK && e == cudaSuccess; ++k)
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+            if (line_z_candidate(k, i) > 0 && fill_lines_ctas_per_sm(k, line_z_candidate(k, i)) <= 0)
                 e = cudaErrorInvalidValue;
     return e;
 }

@@ -48,11 +48,15 @@ struct ProblemDesc {
     int32_t w_corner;            // W(len)
     int32_t len_sum;
     int32_t has_qcorner;         // the fill records the corner's packed key (cross-check)
+    int32_t lzq;                 // line kernel: words per line in a tile's face block
+    int32_t tb_block;            // tile-major layouts: traceback bytes per tile
+    int32_t lst[MSA_MAX_K];      // tile-major layouts: byte stride of axis i inside a tile's block
     int64_t face0_stride;        // column kernel: ints per column in Q (axis-0 faces)
     int64_t face1_stride;        // column kernel: ints per column in aux (axis-1 faces)
     int32_t face0_rows;          // column kernel: skewed rows per axis-0 face
     int32_t face1_rows;          // column kernel: skewed rows per axis-1 face
-    int32_t tb_layout;           // 0: row-major (tbstride); 1: column-blocked (column kernel); 2: tile-major
+    int32_t tb_layout;           // 0: row-major (tbstride); 1: column-blocked (column kernel);
+                                 // 2, 3: tile-major (generic tile kernel, line kernel)
     int32_t pad3;
     const uint8_t *amap;         // device 256-entry char -> code map (0xFF: invalid)
     uint8_t *codes;              // device codes
@@ -117,6 +121,40 @@ __host__ __device__ constexpr int tile_edge_default(int k) {
 __host__ __device__ constexpr bool tile_edge_valid(int k, int edge) {
     return edge > 0 && (tile_edge_candidate(k, 0) == edge || tile_edge_candidate(k, 1) == edge ||
                         tile_edge_candidate(k, 2) == edge);
+}
+
+// Line-sweep kernel geometry shared by the planner and the kernel (k = 4 .. 6;
+// see fill_lines.cuh). A tile is a block of 32 lines over the first k - 1 axes
+// (extents line_ext) times a segment of the last axis of at most Z positions
+// (the compiled candidates below); lane l owns the line whose local coordinates
+// are the mixed-radix digits of l (last line axis fastest) and is skewed by
+// their sum.
+constexpr int kLinesMinK = 4, kLinesMaxK = 6;
+__host__ __device__ constexpr int line_ext(int K, int i) {
+    return K == 4 ? (i == 0 ? 2 : 4)   // 2 x 4 x 4
+         : K == 5 ? (i == 3 ? 4 : 2)   // 2 x 2 x 2 x 4
+                  : 2;                 // k = 6: 2^5
+}
+__host__ __device__ constexpr int line_z_candidate(int k, int idx) {
+    return k == 4 ? (idx == 0 ? 32 : idx == 1 ? 64 : 0)
+         : k == 5 ? (idx == 0 ? 16 : idx == 1 ? 32 : 0)
+         : k == 6 ? (idx == 0 ? 16 : idx == 1 ? 25 : 0)
+                  : 0;
+}
+__host__ __device__ constexpr int line_z_default(int k) { return k == 4 ? 32 : k == 5 ? 32 : 25; }
+__host__ __device__ constexpr bool line_z_valid(int k, int z) {
+    return z > 0 && k >= kLinesMinK && k <= kLinesMaxK &&
+           (line_z_candidate(k, 0) == z || line_z_candidate(k, 1) == z);
+}
+__host__ __device__ constexpr int line_lstride(int K, int i) {  // lane stride of line axis i
+    int s = 1;
+    for (int j = K - 2; j > i; --j) s *= line_ext(K, j);
+    return s;
+}
+__host__ __device__ constexpr int line_skew_max(int K) {
+    int s = 0;
+    for (int i = 0; i < K - 1; ++i) s += line_ext(K, i) - 1;
+    return s;
 }
 
 // k = 3 column kernel geometry (shared by the planner and the kernel).
@@ -211,6 +249,9 @@ int fill_tiles_warps_per_cta(int k, int edge);
 cudaError_t launch_fill_col3(const LaunchDesc &L, int grid, int smem, cudaStream_t s);
 int fill_col3_ctas_per_sm(int smem);
 cudaError_t launch_fill_band2(const LaunchDesc &L, int grid, cudaStream_t s);
+cudaError_t launch_fill_lines(int k, int z, const LaunchDesc &L, int grid, cudaStream_t s);
+int fill_lines_ctas_per_sm(int k, int z);
+int fill_lines_warps_per_cta(int k, int z);
 int fill_band2_ctas_per_sm();
 int fill_band2_warps_per_cta();
 int col3_smem_bytes(int alphabet_size);

@@ -25,6 +25,8 @@ std::mutex g_tune_mu;
 int g_edge[MSA_MAX_K + 1] = {};  // 0: default edge
 bool g_k3_tiles = false;
 bool g_k2_tiles = false;
+int g_line_z[MSA_MAX_K + 1] = {};            // 0: default segment
+bool g_lines_tiles[MSA_MAX_K + 1] = {};      // k = 4 .. 6: prefer the generic tile kernel
 }  // namespace
 
 int tile_edge_for(int k) {
@@ -60,8 +62,36 @@ void set_prefer_tiles_k2(bool v) {
     g_k2_tiles = v;
 }
 
+int line_z_for(int k) {
+    if (k < kLinesMinK || k > kLinesMaxK) return 0;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    return g_line_z[k] ? g_line_z[k] : line_z_default(k);
+}
+
+int set_line_z(int k, int z) {
+    if (k < kLinesMinK || k > kLinesMaxK || (z != 0 && !line_z_valid(k, z))) return MSA_EINVAL;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_line_z[k] = z;
+    return MSA_OK;
+}
+
+bool prefer_tiles_lines(int k) {
+    if (k < kLinesMinK || k > kLinesMaxK) return true;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    return g_lines_tiles[k];
+}
+
+void set_prefer_tiles_lines(int k, bool v) {
+    if (k < kLinesMinK || k > kLinesMaxK) return;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_lines_tiles[k] = v;
+}
+
 int choose_kernel(int k, const int32_t *lens, int A, int requested) {
     if (requested == kKernelTiles) return kKernelTiles;
+    if (k >= kLinesMinK && k <= kLinesMaxK &&
+        (requested == kKernelLines || (requested == kKernelAuto && !prefer_tiles_lines(k))))
+        return kKernelLines;
     if (k == 2 && (requested == kKernelBand2 || (requested == kKernelAuto && !prefer_tiles_k2()))) return kKernelBand2;
     if (col3_fits(k, lens, A) && (requested == kKernelCol3 || !prefer_tiles_k3())) return kKernelCol3;
     return kKernelTiles;
@@ -77,6 +107,13 @@ void tile_extents(int k, const int32_t *lens, int kernel, int edge, int32_t *E) 
     if (kernel == kKernelBand2) {  // bands of 32 rows spanning every column
         E[0] = 32;
         E[1] = lens[1] + 1;
+        return;
+    }
+    if (kernel == kKernelLines) {  // 32-line blocks; the last axis cut into equal segments of at most `edge`
+        for (int i = 0; i < k - 1; ++i) E[i] = line_ext(k, i);
+        const int rho = lens[k - 1] + 1;
+        const int nseg = (rho + edge - 1) / edge;
+        E[k - 1] = (rho + nseg - 1) / nseg;
         return;
     }
     for (int i = 0; i < k; ++i) E[i] = tile_ext(k, edge, i);
@@ -147,11 +184,28 @@ bool score_and_traceback_layout(HostPlan &hp) {
         // tile-major scratch and traceback on the device: tile t's cells form one
         // block of prod(E_i) entries in local row-major order (edge tiles padded)
         int64_t vol = 1;
-        for (int i = 0; i < k; ++i) vol *= hp.E[i];
+        for (int i = k - 1; i >= 0; --i) {
+            hp.lst[i] = (int32_t)vol;
+            vol *= hp.E[i];
+        }
         if (hp.ntiles * vol >= (1LL << 31)) return false;
         hp.qelems = hp.ntiles * vol;
         hp.tb_layout = 2;
+        hp.tb_block = (int32_t)vol;
         hp.tb_dev_bytes = hp.ntiles * vol;
+    }
+    if (hp.kernel == kKernelLines) {
+        // traceback: tile t's block holds (E_{k-1} + skew_max) rows of 32 bytes,
+        // cell (c, z) at (z + sum c_i) * 32 + lane(c); faces: 32 lines of lzq words
+        const int z = hp.E[k - 1];
+        hp.tb_block = (z + line_skew_max(k)) * 32;
+        hp.lst[k - 1] = 32;
+        for (int i = 0; i < k - 1; ++i) hp.lst[i] = 32 + line_lstride(k, i);
+        hp.lzq = (z + 3) / 4 * 4;
+        hp.qelems = hp.ntiles * 32 * hp.lzq;
+        hp.tb_layout = 3;
+        hp.tb_dev_bytes = hp.ntiles * hp.tb_block;
+        if (hp.qelems >= (1LL << 38) || hp.tb_dev_bytes >= (1LL << 40)) return false;
     }
     return true;
 }
@@ -205,6 +259,14 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
         hp.edge = edge < 0 ? tile_edge_for(k) : edge;
         if (!tile_edge_valid(k, hp.edge)) {
             snprintf(buf, sizeof buf, "tile edge %d is not compiled for k=%d", hp.edge, k);
+            err = buf;
+            return MSA_EINVAL;
+        }
+    }
+    if (hp.kernel == kKernelLines) {
+        hp.edge = edge < 0 ? line_z_for(k) : edge;
+        if (!line_z_valid(k, hp.edge)) {
+            snprintf(buf, sizeof buf, "line segment %d is not compiled for k=%d", hp.edge, k);
             err = buf;
             return MSA_EINVAL;
         }

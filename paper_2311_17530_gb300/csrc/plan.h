@@ -10,7 +10,7 @@
 
 namespace msadp {
 
-enum FillKernel { kKernelAuto = 0, kKernelTiles = 1, kKernelCol3 = 2, kKernelBand2 = 3 };
+enum FillKernel { kKernelAuto = 0, kKernelTiles = 1, kKernelCol3 = 2, kKernelBand2 = 3, kKernelLines = 4 };
 
 struct HostPlan {
     int k = 0;
@@ -33,9 +33,13 @@ struct HostPlan {
     int32_t face1_rows = 0;
     int64_t tbstride[MSA_MAX_K] = {};  // row-major strides (the layout msa_plan_read_tb returns)
     int64_t tbbytes = 0;               // row-major size
-    int32_t tb_layout = 0;             // device layout: 0 row-major, 1 column-blocked, 2 tile-major
+    int32_t tb_layout = 0;             // device layout: 0 row-major, 1 column-blocked, 2, 3 tile-major
     int64_t tb_dev_bytes = 0;          // device size of the traceback tensor
-    int32_t edge = 0;              // tile edge of the generic kernel (tile_ext), 0 for the column kernel
+    int32_t tb_block = 0;              // tile-major layouts: bytes per tile
+    int32_t lst[MSA_MAX_K] = {};       // tile-major layouts: byte stride of each axis inside a tile
+    int32_t lzq = 0;                   // line kernel: words per line in a tile's face block
+    int32_t edge = 0;              // tile edge of the generic kernel (tile_ext); longest segment of the
+                                   // line kernel; 0 for the column and band kernels
     int32_t pair_min_sum = 0;
     int32_t w_corner = 0;
     int32_t len_sum = 0;
@@ -56,6 +60,12 @@ void set_prefer_tiles_k3(bool v);
 // k = 2: whether the automatic choice prefers the generic kernel over the band kernel
 bool prefer_tiles_k2();
 void set_prefer_tiles_k2(bool v);
+// k = 4 .. 6: the line kernel's longest segment (0 restores the default) and
+// whether the automatic choice prefers the generic tile kernel over it.
+int line_z_for(int k);
+int set_line_z(int k, int z);
+bool prefer_tiles_lines(int k);
+void set_prefer_tiles_lines(int k, bool v);
 
 // Score scratch and traceback layouts from k, rho, the kernel, tile extents and
 // tile count (row-major, or tile-major for the generic kernel at k >= 4).

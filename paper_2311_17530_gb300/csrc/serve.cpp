@@ -567,6 +567,7 @@ int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg
         L.epoch = epoch_;
         e = g.kernel == kKernelCol3    ? launch_fill_col3(L, g.grid, col3_smem_bytes(g.maxA), s)
           : g.kernel == kKernelBand2 ? launch_fill_band2(L, g.grid, s)
+          : g.kernel == kKernelLines ? launch_fill_lines(g.k, g.edge, L, g.grid, s)
                                      : launch_fill_tiles(g.k, g.edge, L, g.grid, s);
     }
     if (e == cudaSuccess) e = launch_traceback(ddesc, n, &dstate[0].err, dio, IODesc{}, s);

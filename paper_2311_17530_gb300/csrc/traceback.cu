@@ -350,18 +350,19 @@ __device__ void walk_boxes(const ProblemDesc &P, const IODesc &io, unsigned char
 }
 
 // Byte offset of cell x in the traceback tensor: row-major (tbstride), or
-// tile-major (layout 2: tile t = sum (x_i / E_i) gstride_i holds a block of
-// prod E_i bytes in local row-major order).
-__device__ __forceinline__ int64_t tb_cell(const ProblemDesc &P, const int *x, int64_t vol) {
+// tile-major (layouts 2 and 3: tile t = sum (x_i / E_i) gstride_i holds a block
+// of tb_block bytes, the cell at sum_i (x_i mod E_i) * lst_i inside it; layout 2
+// is local row-major, layout 3 the line kernel's skewed rows).
+__device__ __forceinline__ int64_t tb_cell(const ProblemDesc &P, const int *x) {
     int64_t g = 0;
-    if (P.tb_layout == 2) {
+    if (P.tb_layout == 2 || P.tb_layout == 3) {
         int64_t t = 0, loc = 0;
         for (int i = 0; i < P.k; ++i) {
             const int e = P.E[i], q = x[i] / e;
             t += (int64_t)q * P.gstride[i];
-            loc = loc * e + (x[i] - q * e);
+            loc += (int64_t)(x[i] - q * e) * P.lst[i];
         }
-        g = t * vol + loc;
+        g = t * P.tb_block + loc;
     } else {
         for (int i = 0; i < P.k; ++i) g += (int64_t)x[i] * P.tbstride[i];
     }
@@ -376,8 +377,6 @@ __device__ void walk_direct(const ProblemDesc &P, const IODesc &io, unsigned cha
     if (tid >= 32) return;
     int x[MSA_MAX_K];
     for (int i = 0; i < K; ++i) x[i] = ws.x[i];
-    int64_t vol = 1;
-    for (int i = 0; i < K; ++i) vol *= P.E[i];
     int ncols = 0, fail = 0;
     while (!fail && !at_origin(K, x)) {
         // slot 0: the cell itself; slot m: its predecessor x - e_m (if inside)
@@ -388,7 +387,7 @@ __device__ void walk_direct(const ProblemDesc &P, const IODesc &io, unsigned cha
                 c[i] = x[i] - ((m >> i) & 1);
                 in = in && c[i] >= 0;
             }
-            pred[m] = in ? __ldcg(P.tb + tb_cell(P, c, vol)) : (unsigned char)0;
+            pred[m] = in ? __ldcg(P.tb + tb_cell(P, c)) : (unsigned char)0;
         }
         __syncwarp();
         if (tid == 0) {
@@ -411,7 +410,7 @@ __device__ void walk_direct(const ProblemDesc &P, const IODesc &io, unsigned cha
     }
 }
 
-// Tile-major layout (k >= 4): the CTA stages the blocks of the tiles
+// Tile-major layouts (k >= 4): the CTA stages the blocks of the tiles
 // [q - span + 1, q] per axis around the current cell's tile q (span 4, 3 or 2:
 // the largest whose blocks fit the window memory), one 16-byte-aligned copy of
 // each block, and thread 0 walks them in registers -- local coordinates, the
@@ -421,12 +420,11 @@ template <int K>
 __device__ void walk_tiles(const ProblemDesc &P, const IODesc &io, unsigned char *smem, WalkState &ws) {
     const int tid = threadIdx.x;
     int E[K], lst[K];
-    int vol = 1;
-    for (int i = K - 1; i >= 0; --i) {
+    for (int i = 0; i < K; ++i) {
         E[i] = P.E[i];
-        lst[i] = vol;
-        vol *= E[i];
+        lst[i] = P.lst[i];
     }
+    const int vol = P.tb_block;                // bytes of one tile's block
     const int slot = round_up(vol + 15, 16);  // a block copied from the 16-byte boundary below it
     const int cps = slot / 16;
     int span = 0, nslot = 0;
@@ -611,15 +609,15 @@ __global__ void __launch_bounds__(kTbThreads) traceback_kernel(const ProblemDesc
         walk_boxes<2>(P, io, smem, ws);
     else if (K == 3)
         walk_boxes<3>(P, io, smem, ws);
-    else if (P.tb_layout == 2 && K == 4)
+    else if (P.tb_layout >= 2 && K == 4)
         walk_tiles<4>(P, io, smem, ws);
-    else if (P.tb_layout == 2 && K == 5)
+    else if (P.tb_layout >= 2 && K == 5)
         walk_tiles<5>(P, io, smem, ws);
-    else if (P.tb_layout == 2 && K == 6)
+    else if (P.tb_layout >= 2 && K == 6)
         walk_tiles<6>(P, io, smem, ws);
-    else if (P.tb_layout == 2 && K == 7)
+    else if (P.tb_layout >= 2 && K == 7)
         walk_tiles<7>(P, io, smem, ws);
-    else if (P.tb_layout == 2 && K == 8)
+    else if (P.tb_layout >= 2 && K == 8)
         walk_tiles<8>(P, io, smem, ws);
     else
         walk_direct(P, io, smem, ws);

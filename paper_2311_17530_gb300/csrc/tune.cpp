@@ -1,7 +1,7 @@
 // Autotuner of the tile shape: the paper fixes its partition size S by hand
 // (section 3.2's example uses S = 3); here each k has a few compiled tile edges
 // (tile_edge_candidate) and, for k = 3, the column kernel (k = 2: the band
-// kernel). msa_autotune times
+// kernel; k = 4 .. 6: the line kernel's compiled segment lengths). msa_autotune times
 // every candidate on a synthetic problem of the caller's shape -- plan creation,
 // then repeated executions of encode, fill and traceback between CUDA events --
 // and makes the fastest the choice for k in every later plan and serving batch.
@@ -36,7 +36,7 @@ int time_candidate(int k, const int32_t *lens, const char *alphabet, int kernel,
     msa_plan_info info;
     msa_plan_get_info(plan, &info);
     *out_kernel = info.fill_kernel;
-    *out_edge = info.fill_kernel == kKernelTiles ? edge : 0;
+    *out_edge = info.fill_kernel == kKernelTiles || info.fill_kernel == kKernelLines ? edge : 0;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -76,6 +76,18 @@ int msa_set_tile_edge(int k, int32_t edge) {
 int msa_get_tile_edge(int k, int32_t *out_edge) {
     if (k < 2 || k > MSA_MAX_K || !out_edge) return set_error(MSA_EINVAL, "bad arguments");
     *out_edge = tile_edge_for(k);
+    return MSA_OK;
+}
+
+int msa_set_line_segment(int k, int32_t z) {
+    if (set_line_z(k, z) != MSA_OK) return set_error(MSA_EINVAL, "line segment %d is not compiled for k=%d", z, k);
+    if (z == 0) set_prefer_tiles_lines(k, false);  // defaults: the line kernel for k = 4 .. 6
+    return MSA_OK;
+}
+
+int msa_get_line_segment(int k, int32_t *out_z) {
+    if (k < 2 || k > MSA_MAX_K || !out_z) return set_error(MSA_EINVAL, "bad arguments");
+    *out_z = line_z_for(k);
     return MSA_OK;
 }
 
@@ -127,12 +139,15 @@ int msa_autotune(int k, const int32_t *lens, int alphabet_size, int32_t repeats,
         if (tile_edge_candidate(k, i) > 0) cands.push_back({kKernelTiles, tile_edge_candidate(k, i)});
     if (k == 3 && choose_kernel(k, lens, alphabet_size, kKernelCol3) == kKernelCol3) cands.push_back({kKernelCol3, 0});
     if (k == 2) cands.push_back({kKernelBand2, 0});
+    for (int i = 0; i < 2; ++i)
+        if (line_z_candidate(k, i) > 0) cands.push_back({kKernelLines, line_z_candidate(k, i)});
     int best = -1;
     for (const Cand &c : cands) {
         if (out->ncand >= MSA_MAX_TUNING_CANDIDATES) break;
         float ms = 0;
         int kern = 0, edge = 0;
-        rc = time_candidate(k, lens, alphabet, c.kernel, c.kernel == kKernelTiles ? c.edge : -1, b, -8, repeats, s,
+        rc = time_candidate(k, lens, alphabet, c.kernel, c.kernel == kKernelTiles || c.kernel == kKernelLines ? c.edge : -1,
+                            b, -8, repeats, s,
                             &ms, &kern, &edge);
         if (rc) return rc;
         const int i = out->ncand++;
@@ -147,9 +162,14 @@ int msa_autotune(int k, const int32_t *lens, int alphabet_size, int32_t repeats,
         set_tile_edge(k, out->cand_edge[best]);
         if (k == 3) set_prefer_tiles_k3(true);
         if (k == 2) set_prefer_tiles_k2(true);
+        set_prefer_tiles_lines(k, true);
     } else {
         if (k == 3) set_prefer_tiles_k3(false);
         if (k == 2) set_prefer_tiles_k2(false);
+        if (out->cand_kernel[best] == kKernelLines) {
+            set_line_z(k, out->cand_edge[best]);
+            set_prefer_tiles_lines(k, false);
+        }
         // the best generic edge stays the fallback for shapes the column kernel cannot take
         int bt = -1;
         for (int i = 0; i < out->ncand; ++i)

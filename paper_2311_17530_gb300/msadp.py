@@ -32,7 +32,8 @@ EXPORTED = ["msa_align", "msa_last_error", "msa_set_stream", "msa_config", "msa_
             "msa_plan_execute", "msa_plan_get_info", "msa_plan_destroy", "msa_submit", "msa_poll",
             "msa_cancel", "msa_drain", "msa_wave_sizes", "msa_tile_shape", "msa_version",
             "msa_plan_read_tb", "msa_plan_timings", "msa_align_noalloc", "msa_wait_any",
-            "msa_set_tile_edge", "msa_get_tile_edge", "msa_autotune"]
+            "msa_set_tile_edge", "msa_get_tile_edge", "msa_set_line_segment", "msa_get_line_segment",
+            "msa_autotune"]
 
 
 class MsaError(RuntimeError):
@@ -100,6 +101,8 @@ def library() -> ctypes.CDLL:
     L.msa_wait_any.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
     L.msa_set_tile_edge.argtypes = [ctypes.c_int, ctypes.c_int32]
     L.msa_get_tile_edge.argtypes = [ctypes.c_int, i32p]
+    L.msa_set_line_segment.argtypes = [ctypes.c_int, ctypes.c_int32]
+    L.msa_get_line_segment.argtypes = [ctypes.c_int, i32p]
     L.msa_autotune.argtypes = [ctypes.c_int, i32p, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(Tuning)]
     L.msa_wave_sizes.argtypes = [ctypes.c_int, i32p, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32, i32p]
     L.msa_tile_shape.argtypes = [ctypes.c_int, i32p, i32p, i32p]
@@ -291,12 +294,22 @@ def msa_get_tile_edge(k: int) -> int:
     return int(e.value)
 
 
+def msa_set_line_segment(k: int, z: int) -> None:
+    _check(library().msa_set_line_segment(int(k), int(z)))
+
+
+def msa_get_line_segment(k: int) -> int:
+    z = ctypes.c_int32(0)
+    _check(library().msa_get_line_segment(int(k), ctypes.byref(z)))
+    return int(z.value)
+
+
 def msa_autotune(lens: Sequence[int], alphabet_size: int, repeats: int = 3) -> dict:
-    """Time the compiled tile shapes (and the k=3 column or k=2 band kernel) for this shape; the
-    fastest becomes the choice for k. Returns the candidates and the choice."""
+    """Time the compiled tile shapes (and the k=3 column, k=2 band or k=4..6 line kernel) for this
+    shape; the fastest becomes the choice for k. Returns the candidates and the choice."""
     t = Tuning()
     _check(library().msa_autotune(len(lens), _i32(lens), int(alphabet_size), int(repeats), ctypes.byref(t)))
-    names = {1: "tiles", 2: "column", 3: "band"}
+    names = {1: "tiles", 2: "column", 3: "band", 4: "lines"}
     cands = [{"kernel": names[int(t.cand_kernel[i])], "edge": int(t.cand_edge[i]),
               "ms": float(t.cand_ms[i])} for i in range(t.ncand)]
     return {"k": int(t.k), "lens": list(lens), "candidates": cands, "best": cands[t.best]}

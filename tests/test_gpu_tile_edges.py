@@ -24,6 +24,8 @@ def restore():
     msa.msa_config("fill_kernel", 0)
     for k in CANDIDATES:
         msa.msa_set_tile_edge(k, 0)
+    for k in (4, 5, 6):
+        msa.msa_set_line_segment(k, 0)
 
 
 def run(p):
@@ -69,8 +71,15 @@ def test_autotune_picks_the_fastest_and_plans_follow():
     finally:
         plan.close()
     res4 = msa.msa_autotune([30, 32, 34, 36], 4, repeats=2)
-    assert {c["edge"] for c in res4["candidates"]} == {4, 5, 6}
-    assert msa.msa_get_tile_edge(4) == res4["best"]["edge"]
+    assert {(c["kernel"], c["edge"]) for c in res4["candidates"]} == {("tiles", 4), ("tiles", 5), ("tiles", 6),
+                                                                      ("lines", 32), ("lines", 64)}
+    best4 = res4["best"]
+    if best4["kernel"] == "tiles":
+        assert msa.msa_get_tile_edge(4) == best4["edge"]
+    else:
+        assert msa.msa_get_line_segment(4) == best4["edge"]
+    with msa.Plan(4, [30, 32, 34, 36], inputs.DNA) as plan4:
+        assert plan4.info().fill_kernel == (1 if best4["kernel"] == "tiles" else 4)
     # the tuned shape still gives the oracle's answer
     p = inputs.random_problem(3100, 4, [14, 17, 15, 13], related=True)
     want = oracle.align(p.seqs, p.alphabet, p.subst, p.gap)
