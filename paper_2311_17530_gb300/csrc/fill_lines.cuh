@@ -196,24 +196,32 @@ __global__ void __launch_bounds__(line_best_warps<K, Z>() * 32) fill_lines_kerne
         skew += cl[i];
     }
 
+    // The next ticket is taken while the current tile runs, so its atomic (an L2
+    // round trip) is off the tile's path; a warp holding an unstarted ticket only
+    // delays tiles with later tickets, never one it waits for.
+    int tnext = 0;
+    if (lane == 0) tnext = atomicAdd(L.ticket, 1);
+    int cached_prob = -1;
+    bool cached_live = false;
     while (true) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(L.ticket, 1);
-        t = __shfl_sync(kFull, t, 0);
+        const int t = __shfl_sync(kFull, tnext, 0);
         if ((int64_t)t >= L.ntickets) break;
         if (ld_volatile(L.err) != 0) break;
+        if (lane == 0) tnext = atomicAdd(L.ticket, 1);
         const uint64_t ent = L.order[t];
-        const ProblemDesc &P = L.probs[(int)(ent >> 32)];
+        const int pidx = (int)(ent >> 32);
+        const ProblemDesc &P = L.probs[pidx];
         const int64_t lin = (int64_t)(uint32_t)ent;
 
         int tco[K], o[K];
         {
-            int64_t rem = lin;
+            // tile coordinates (32-bit: a problem has fewer than 2^31 tiles)
+            unsigned rem = (unsigned)lin;
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-                const int64_t gs = P.gstride[j];
+                const unsigned gs = (unsigned)P.gstride[j];
                 tco[j] = (int)(rem / gs);
-                rem -= tco[j] * gs;
+                rem -= (unsigned)tco[j] * gs;
                 o[j] = tco[j] * P.E[j];
             }
         }
@@ -221,7 +229,12 @@ __global__ void __launch_bounds__(line_best_warps<K, Z>() * 32) fill_lines_kerne
         // Everything that does not depend on the face predecessors comes first, so
         // that its loads overlap the wait: problem fields, the neighbour table, the
         // sweep axis's pair tables and this line's pair sums.
-        const bool live = ld_volatile(&P.istat->status) == 0;
+        // the encode step's verdict on the problem (fixed before the fill starts)
+        if (pidx != cached_prob) {
+            cached_prob = pidx;
+            cached_live = ld_volatile(&P.istat->status) == 0;
+        }
+        const bool live = cached_live;
         const int A = P.A;
         const int32_t *__restrict__ tab = P.tab;
         const uint8_t *__restrict__ codes = P.codes;
@@ -244,51 +257,66 @@ __global__ void __launch_bounds__(line_best_warps<K, Z>() * 32) fill_lines_kerne
                     }
                 nb[S] = in ? (int)n : -1;
             }
-            // pair tables of the sweep axis: PT[i][a][z] = tab(code_i(o_i + a), code_s(z0 + z))
+            // Pair tables of the sweep axis, PT[i][a][z] = tab(code_i(o_i + a), code_s(z0 + z)),
+            // and this line's pair sums over subsets of the line axes (constant
+            // along the line). All residue codes are loaded first, then all table
+            // entries, so the set-up costs two dependent round trips.
+            constexpr int NR = (Z + 31) / 32;  // positions per lane
+            constexpr int NROW = [] {
+                int n = 0;
+                for (int i = 0; i < K - 1; ++i) n += line_ext(K, i);
+                return n;
+            }();
+            int cz[NR], ca[NROW], cd[NA];
             {
-                const int lens = P.len[NA];
-                int cz[(Z + 31) / 32];
+                const int lens = P.len[NA], cofs = P.cofs[NA];
 #pragma unroll
-                for (int r = 0; r < (Z + 31) / 32; ++r) {
+                for (int r = 0; r < NR; ++r) {
                     const int x = z0 + lane + 32 * r;
-                    cz[r] = (x >= 1 && x <= lens) ? codes[P.cofs[NA] + x - 1] : 0;
+                    cz[r] = (x >= 1 && x <= lens) ? codes[cofs + x - 1] : 0;
                 }
-                int pb = 0;
+                int row = 0;
 #pragma unroll
                 for (int i = 0; i < NA; ++i) {
+                    const int len = P.len[i], cof = P.cofs[i];
 #pragma unroll
                     for (int a = 0; a < line_ext(K, i); ++a) {
                         const int x = o[i] + a;
-                        const int ca = (x >= 1 && x <= P.len[i]) ? codes[P.cofs[i] + x - 1] : 0;
-#pragma unroll
-                        for (int r = 0; r < (Z + 31) / 32; ++r) {
-                            const int z = lane + 32 * r;
-                            if (z < Zt) PT[pb + a * ZS + z] = __ldg(tab + ca * A + cz[r]);
-                        }
+                        ca[row++] = (x >= 1 && x <= len) ? codes[cof + x - 1] : 0;
                     }
+                    const int x = o[i] + cl[i];
+                    cd[i] = (x >= 1 && x <= len) ? codes[cof + x - 1] : 0;
+                }
+            }
+            int pt[NROW][NR];
+#pragma unroll
+            for (int row = 0; row < NROW; ++row)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) pt[row][r] = __ldg(tab + ca[row] * A + cz[r]);
+            {
+                int row = 0, pb = 0;
+#pragma unroll
+                for (int i = 0; i < NA; ++i) {
+#pragma unroll
+                    for (int a = 0; a < line_ext(K, i); ++a, ++row)
+#pragma unroll
+                        for (int r = 0; r < NR; ++r) {
+                            const int z = lane + 32 * r;
+                            if (z < Zt) PT[pb + a * ZS + z] = pt[row][r];
+                        }
                     pb += line_ext(K, i) * ZS;
                 }
             }
-            // pair sums of this line's subsets (pairs among line axes; constant along the line)
-            {
-                int cd[NA];
+            Sp[0] = 0;
 #pragma unroll
-                for (int i = 0; i < NA; ++i) {
-                    const int x = o[i] + cl[i];
-                    cd[i] = (x >= 1 && x <= P.len[i]) ? codes[P.cofs[i] + x - 1] : 0;
-                }
-                Sp[0] = 0;
+            for (int h = 0; h < NA; ++h) {
+                // R[r] = sum over l in r of pair(l, h), r a subset of the axes below h
+                int R[1 << (NA - 1)];
+                R[0] = 0;
 #pragma unroll
-                for (int h = 0; h < NA; ++h) {
-                    // R[r] = sum over l in r of pair(l, h), r a subset of the axes below h
-                    int R[1 << (NA - 1)];
-                    R[0] = 0;
+                for (int r = 1; r < (1 << h); ++r) R[r] = R[r & (r - 1)] + __ldg(tab + cd[lowbit_c(r)] * A + cd[h]);
 #pragma unroll
-                    for (int r = 1; r < (1 << h); ++r)
-                        R[r] = R[r & (r - 1)] + __ldg(tab + cd[lowbit_c(r)] * A + cd[h]);
-#pragma unroll
-                    for (int r = 0; r < (1 << h); ++r) Sp[r | (1 << h)] = Sp[r] + R[r];
-                }
+                for (int r = 0; r < (1 << h); ++r) Sp[r | (1 << h)] = Sp[r] + R[r];
             }
         }
         __syncwarp();  // nb and PT are read by every lane below
@@ -302,7 +330,9 @@ __global__ void __launch_bounds__(line_best_warps<K, Z>() * 32) fill_lines_kerne
             if (lane == 0) atomicCAS(L.err, 0, MSA_ETIMEOUT);
             break;
         }
-        __threadfence();
+        // The acquiring lanes' loads precede every lane's loads below: the warp
+        // barrier orders them (no full fence needed).
+        __syncwarp();
 
         if (live) {
             const int32_t *__restrict__ Qg = P.Q;
@@ -311,7 +341,22 @@ __global__ void __launch_bounds__(line_best_warps<K, Z>() * 32) fill_lines_kerne
             // halo'd line's position -1 from the tile below along the sweep axis.
             // Loads bypass L1 (other SMs wrote them) and are issued in batches.
             {
-                constexpr int HB = 8;
+                // position -1 of every halo'd line from the tile below along the sweep axis
+                constexpr int NZF = (NHL + 31) / 32;
+                const bool below = tco[NA] > 0;
+                const int64_t gsz = P.gstride[NA];
+                int zf[NZF];
+#pragma unroll
+                for (int u = 0; u < NZF; ++u) {
+                    const int j = lane + 32 * u;
+                    zf[u] = kNeg;
+                    if (j < NHL) {
+                        const uint32_t e = htab[j];
+                        const int src = nb[e >> 19];
+                        if (below && src >= 0) zf[u] = __ldcg(Qg + (src - gsz) * QB + (int)((e >> 14) & 31) * ZQ + (Ez - 1));
+                    }
+                }
+                constexpr int HB = K >= 6 ? 8 : 16;  // loads in flight per lane (registers bound it at k = 6)
                 for (int i0 = 0; i0 < NH * NQ; i0 += 32 * HB) {
                     int4 val[HB];
                     int dst[HB];
@@ -341,14 +386,10 @@ __global__ void __launch_bounds__(line_best_warps<K, Z>() * 32) fill_lines_kerne
                             if (n > 3) V[dst[u] + 3] = val[u].w;
                         }
                 }
-                const bool below = tco[NA] > 0;
-                const int64_t gsz = P.gstride[NA];
-                for (int j = lane; j < NHL; j += 32) {
-                    const uint32_t e = htab[j];
-                    const int src = nb[e >> 19];
-                    int v = kNeg;
-                    if (below && src >= 0) v = __ldcg(Qg + (src - gsz) * QB + (int)((e >> 14) & 31) * ZQ + (Ez - 1));
-                    V[e & 0x3FFF] = v;
+#pragma unroll
+                for (int u = 0; u < NZF; ++u) {
+                    const int j = lane + 32 * u;
+                    if (j < NHL) V[htab[j] & 0x3FFF] = zf[u];
                 }
             }
             __syncwarp();
@@ -443,11 +484,10 @@ __global__ void __launch_bounds__(line_best_warps<K, Z>() * 32) fill_lines_kerne
                 if (corner && zc >= 0 && zc < Zt) *P.qcorner = V[lb + 1 + zc];
             }
         }
+        // Every lane's stores precede lane 0's release through the warp barrier;
+        // the release store makes them visible with the flag.
         __syncwarp();
-        if (lane == 0 && (int64_t)t != L.withhold) {
-            __threadfence();
-            st_release(&L.done[tile_base + lin], 1);
-        }
+        if (lane == 0 && (int64_t)t != L.withhold) st_release(&L.done[tile_base + lin], 1);
     }
 }
 
