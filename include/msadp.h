@@ -290,7 +290,7 @@ int msa_get_tile_edge(int k, int32_t *out_edge);
 /*
  * Longest segment of the last axis that one tile of the line kernel (k = 4..6)
  * sweeps; the planner cuts the axis into equal segments no longer than this.
- * Only compiled lengths are accepted (k=4: 32 64; k=5: 16 32; k=6: 16 25); 0
+ * Only compiled lengths are accepted (k=4: 8 16 32; k=5: 16 32; k=6: 16 25); 0
  * restores the default (32, 32, 25) and the automatic choice of the line kernel
  * for k = 4..6. Later plans and serving batches use the setting. Host-only,
  * thread-safe; MSA_EINVAL for other k or lengths.

@@ -124,7 +124,7 @@ int persistent_grid(int k, int kernel, int64_t units, int A, int edge) {
     {
         std::lock_guard<std::mutex> g(mu);
         const int sub = kernel == kKernelCol3    ? A
-                      : kernel == kKernelLines ? (edge == line_z_candidate(k, 0) ? 1 : 2)
+                      : kernel == kKernelLines ? (edge == line_z_candidate(k, 0) ? 1 : edge == line_z_candidate(k, 1) ? 2 : 3)
                                                : (edge & 31);
         int &slot = cache[kernel][k][sub];
         if (!slot) {

@@ -171,7 +171,7 @@ cudaError_t prepare_kernel_attributes() {
             if (tile_edge_candidate(k, i) > 0 && fill_tiles_ctas_per_sm(k, tile_edge_candidate(k, i)) <= 0)
                 e = cudaErrorInvalidValue;
     for (int k = kLinesMinK; k <= kLinesMaxK && e == cudaSuccess; ++k)
-        for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        for (int i = 0; i < kMaxLineSegments && e == cudaSuccess; ++i)
             if (line_z_candidate(k, i) > 0 && fill_lines_ctas_per_sm(k, line_z_candidate(k, i)) <= 0)
                 e = cudaErrorInvalidValue;
     return e;

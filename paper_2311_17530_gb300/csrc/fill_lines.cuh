@@ -59,10 +59,10 @@ namespace msadp {
 // offsets sum_i c_i (A_i - 1) distinct mod 32, and the smallest footprint
 // (within 7 % of the unpadded box).
 __host__ __device__ constexpr int line_stride(int K, int Z, int i) {
-    constexpr int k4z32[] = {34, 103, 521}, k4z64[] = {66, 199, 1001};
+    constexpr int k4z8[] = {45, 9, 136}, k4z16[] = {17, 52, 261}, k4z32[] = {34, 103, 521};
     constexpr int k5z16[] = {17, 256, 777, 51}, k5z32[] = {34, 103, 1553, 309};
     constexpr int k6z16[] = {17, 51, 153, 460, 1381}, k6z25[] = {26, 79, 237, 713, 2161};
-    return K == 4 ? (Z == 32 ? k4z32[i] : k4z64[i])
+    return K == 4 ? (Z == 8 ? k4z8[i] : Z == 16 ? k4z16[i] : k4z32[i])
          : K == 5 ? (Z == 16 ? k5z16[i] : k5z32[i])
                   : (Z == 16 ? k6z16[i] : k6z25[i]);
 }
@@ -523,15 +523,27 @@ int lines_ctas() {
 // Dispatch of one k over its compiled segment lengths (instantiated in fill_lines_k<k>.cu).
 template <int K>
 struct LinesK {
-    static constexpr int Z0 = line_z_candidate(K, 0), Z1 = line_z_candidate(K, 1);
+    static constexpr int Z0 = line_z_candidate(K, 0), Z1 = line_z_candidate(K, 1), Z2 = line_z_candidate(K, 2);
     static cudaError_t launch(int z, const LaunchDesc &L, int grid, cudaStream_t s) {
         if (z == Z0) return launch_lines<K, Z0>(L, grid, s);
         if (z == Z1) return launch_lines<K, Z1>(L, grid, s);
+        if constexpr (Z2 > 0)
+            if (z == Z2) return launch_lines<K, Z2>(L, grid, s);
         return cudaErrorInvalidValue;
     }
-    static int ctas(int z) { return z == Z0 ? lines_ctas<K, Z0>() : z == Z1 ? lines_ctas<K, Z1>() : 0; }
+    static int ctas(int z) {
+        if (z == Z0) return lines_ctas<K, Z0>();
+        if (z == Z1) return lines_ctas<K, Z1>();
+        if constexpr (Z2 > 0)
+            if (z == Z2) return lines_ctas<K, Z2>();
+        return 0;
+    }
     static int warps(int z) {
-        return z == Z0 ? line_best_warps<K, Z0>() : z == Z1 ? line_best_warps<K, Z1>() : 0;
+        if (z == Z0) return line_best_warps<K, Z0>();
+        if (z == Z1) return line_best_warps<K, Z1>();
+        if constexpr (Z2 > 0)
+            if (z == Z2) return line_best_warps<K, Z2>();
+        return 0;
     }
 };
 

@@ -135,8 +135,9 @@ __host__ __device__ constexpr int line_ext(int K, int i) {
          : K == 5 ? (i == 3 ? 4 : 2)   // 2 x 2 x 2 x 4
                   : 2;                 // k = 6: 2^5
 }
+constexpr int kMaxLineSegments = 3;
 __host__ __device__ constexpr int line_z_candidate(int k, int idx) {
-    return k == 4 ? (idx == 0 ? 32 : idx == 1 ? 64 : 0)
+    return k == 4 ? (idx == 0 ? 8 : idx == 1 ? 16 : idx == 2 ? 32 : 0)
          : k == 5 ? (idx == 0 ? 16 : idx == 1 ? 32 : 0)
          : k == 6 ? (idx == 0 ? 16 : idx == 1 ? 25 : 0)
                   : 0;
@@ -144,7 +145,7 @@ __host__ __device__ constexpr int line_z_candidate(int k, int idx) {
 __host__ __device__ constexpr int line_z_default(int k) { return k == 4 ? 32 : k == 5 ? 32 : 25; }
 __host__ __device__ constexpr bool line_z_valid(int k, int z) {
     return z > 0 && k >= kLinesMinK && k <= kLinesMaxK &&
-           (line_z_candidate(k, 0) == z || line_z_candidate(k, 1) == z);
+           (line_z_candidate(k, 0) == z || line_z_candidate(k, 1) == z || line_z_candidate(k, 2) == z);
 }
 __host__ __device__ constexpr int line_lstride(int K, int i) {  // lane stride of line axis i
     int s = 1;

@@ -139,7 +139,7 @@ int msa_autotune(int k, const int32_t *lens, int alphabet_size, int32_t repeats,
         if (tile_edge_candidate(k, i) > 0) cands.push_back({kKernelTiles, tile_edge_candidate(k, i)});
     if (k == 3 && choose_kernel(k, lens, alphabet_size, kKernelCol3) == kKernelCol3) cands.push_back({kKernelCol3, 0});
     if (k == 2) cands.push_back({kKernelBand2, 0});
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < kMaxLineSegments; ++i)
         if (line_z_candidate(k, i) > 0) cands.push_back({kKernelLines, line_z_candidate(k, i)});
     int best = -1;
     for (const Cand &c : cands) {

@@ -13,11 +13,11 @@ from paper_2311_17530_gb300 import msadp
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-SEGMENTS = {4: [32, 64], 5: [16, 32], 6: [16, 25]}
+SEGMENTS = {4: [8, 16, 32], 5: [16, 32], 6: [16, 25]}
 # line blocks are 2x4x4 (k=4), 2x2x2x4 (k=5), 2^5 (k=6); every shape covers several
 # blocks per line axis with a ragged tail and at least two segments of the last axis
 SHAPES = {
-    (4, 32): [9, 13, 10, 70], (4, 64): [7, 9, 8, 139],
+    (4, 8): [9, 13, 10, 30], (4, 16): [9, 13, 10, 40], (4, 32): [9, 13, 10, 70],
     (5, 16): [5, 4, 5, 9, 40], (5, 32): [3, 4, 3, 9, 70],
     (6, 16): [4, 3, 4, 3, 4, 30], (6, 25): [3, 4, 3, 4, 3, 52],
 }

@@ -72,7 +72,7 @@ def test_autotune_picks_the_fastest_and_plans_follow():
         plan.close()
     res4 = msa.msa_autotune([30, 32, 34, 36], 4, repeats=2)
     assert {(c["kernel"], c["edge"]) for c in res4["candidates"]} == {("tiles", 4), ("tiles", 5), ("tiles", 6),
-                                                                      ("lines", 32), ("lines", 64)}
+                                                                      ("lines", 8), ("lines", 16), ("lines", 32)}
     best4 = res4["best"]
     if best4["kernel"] == "tiles":
         assert msa.msa_get_tile_edge(4) == best4["edge"]
