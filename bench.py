@@ -44,7 +44,15 @@ import inputs  # noqa: E402
 METRIC = "DP cells/s"
 UNIT = "cells/s"
 SMS_GB300 = 152
-INT32_LANES_PER_SM = 128  # 4 SM sub-partitions x 32 lanes: IADD/IMNMX issue at full rate (measured)
+# One 32-bit integer operation per issue slot: 4 SM sub-partitions x 32 lanes per clock.
+# Integer adds issue at this rate; the max family (IMNMX, the three-input VIMNMX3 and the
+# fused add-max VIADDMNMX) at half of it, each fused form doing two operations
+# (tests/alu_peak_probe.cu under ncu).
+INT32_LANES_PER_SM = 128
+PEAK_BASIS = ("{sms} SMs x 4 issue slots x 32 lanes x {mhz:.0f} MHz: one 32-bit integer op per issue slot "
+              "(adds full rate, maxes half rate but fused pairs count two)")
+# the benchmark's workloads besides the headline one
+PER_WORKLOADS = ("pr1", "k2_protein", "k3_protein", "k4_dna", "k6_protein")
 SM_MAX_MHZ_FALLBACK = 2070.0
 
 
@@ -386,22 +394,20 @@ def run_reference(args, rank, world):
     return 0
 
 
-def run_gb300(args, rank, world, local):
+# CPU-baseline sample per workload (cells): about 1-10 s of the oracle on one core
+PER_WORKLOAD_CPU_CELLS = {"pr1": 2.2e6, "k2_protein": 1.0e8, "k3_protein": 1.2e8, "k4_dna": 2.0e7,
+                          "k6_protein": 5.0e6}
+
+
+def measure_workload(name, steps, warmup, args, dist, dev, sms, world, rank, clocks=None, cpu_cells=None):
+    """One workload's device-timed steps, fill-kernel roofline, end-to-end rate
+    through msa_align and (rank 0, one GPU) the oracle's CPU sample."""
     import torch
 
     from paper_2311_17530_gb300 import msadp
-
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    dev = torch.device("cuda", local)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    p = inputs.WORKLOADS[args.workload]()
+    p = inputs.WORKLOADS[name]()
     total_len = sum(p.lens)
-    # the autotuner picks the tile shape (and for k = 3 the kernel) for this shape,
-    # unless a tile edge is given
+    # the autotuner picks the kernel and tile shape for this shape, unless a tile edge is given
     if args.tile_edge:
         msadp.msa_set_tile_edge(p.k, args.tile_edge)
         msadp.msa_config("fill_kernel", 1)
@@ -422,18 +428,18 @@ def run_gb300(args, rank, world, local):
     flush = p.cells < l2_bytes
     scratch = torch.empty(2 * l2_bytes // 4, dtype=torch.int32, device=dev) if flush else None
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
     score, rows, status = msadp.decode_device_result(d_result, d_masks, p.seqs)
     if status != 0:
-        raise SystemExit(f"device status {status}")
-    golden = os.path.join(ROOT, "tests", "golden", f"{args.workload}.json")
+        raise SystemExit(f"{name}: device status {status}")
+    golden = os.path.join(ROOT, "tests", "golden", f"{name}.json")
     checked = None
     if os.path.exists(golden):
         checked = json.load(open(golden))["score"] == score
         if not checked:
-            raise SystemExit(f"score {score} differs from the stored oracle value")
+            raise SystemExit(f"{name}: score {score} differs from the stored oracle value")
 
     msadp.msa_config("timing", 1)
     try:
@@ -443,11 +449,11 @@ def run_gb300(args, rank, world, local):
     if dist:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    clocks = ClockSampler(local)
-    clocks.start()
+    if clocks is not None:
+        clocks.start()
     if flush:
         evs = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             scratch.fill_(1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -460,12 +466,11 @@ def run_gb300(args, rank, world, local):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             step()
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         ms_total = ev0.elapsed_time(ev1)
-    clk = clocks.stop()
     msadp.msa_config("timing", 0)
     enc_ms, fill_ms, tb_ms = plan.timings()
     # the fill kernel alone: median over 20 further executions, one at a time
@@ -481,16 +486,16 @@ def run_gb300(args, rank, world, local):
     ms_total = max_over_ranks(ms_total, dist, dev)
     if dist:
         dist.barrier()
-    ms_step = ms_total / args.steps
+    ms_step = ms_total / steps
     value = whole_job_rate(p.cells, world, ms_step / 1e3)
 
     # end to end through the public C-ABI with host buffers
     e2e = None
     if not args.no_e2e:
-        for _ in range(max(1, args.warmup)):
+        for _ in range(max(1, warmup)):
             msadp.msa_align(p.seqs, p.alphabet, p.subst, p.gap)
         ts = []
-        for _ in range(args.steps):
+        for _ in range(steps):
             if flush:
                 scratch.fill_(1)
                 torch.cuda.synchronize(dev)
@@ -499,20 +504,63 @@ def run_gb300(args, rank, world, local):
             ts.append(time.perf_counter() - t0)
             assert s2 == score
         tot = max_over_ranks(sum(ts), dist, dev)
-        e2e = {"value": whole_job_rate(p.cells * args.steps, world, tot), "unit": UNIT,
+        e2e = {"value": whole_job_rate(p.cells * steps, world, tot), "unit": UNIT,
                "h2d_bytes_per_step": total_len + p.subst.size * 4,
-               "d2h_bytes_per_step": 16 + total_len, "ms_per_step": 1e3 * tot / args.steps}
+               "d2h_bytes_per_step": 16 + total_len, "ms_per_step": 1e3 * tot / steps}
 
     kernel = {1: "fill_tiles", 2: "fill_col3", 3: "fill_band2", 4: "fill_lines"}[int(info.fill_kernel)]
     ops = alg_ops_per_cell(p.k) * p.cells
     achieved = ops / (fill_ms / 1e3) / 1e12
     peak = alu_peak_tiops(sms)
     roofline = {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TIOP/s",
-                "frac": achieved / peak, "traffic": measured_traffic(args.workload, kernel),
+                "frac": achieved / peak, "traffic": measured_traffic(name, kernel),
                 "ops_per_cell": alg_ops_per_cell(p.k), "fill_ms": fill_ms,
                 "fill_ms_median_of_20": statistics.median(fill_runs), "encode_ms": enc_ms,
-                "traceback_ms": tb_ms,
-                "peak_basis": f"{sms} SMs x {INT32_LANES_PER_SM} INT32 lanes x {sm_max_mhz():.0f} MHz"}
+                "traceback_ms": tb_ms, "peak_basis": PEAK_BASIS.format(sms=sms, mhz=sm_max_mhz())}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        q, dt = time_oracle(p, cpu_cells if cpu_cells is not None else PER_WORKLOAD_CPU_CELLS.get(name, 2e7))
+        cpu = {"value": q.cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle on prefixes {q.lens} of {p.name} ({q.cells} cells, {dt:.1f} s)"}
+    out = {"value": value, "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": ms_step,
+           "config": {"workload": p.name, "k": p.k, "lens": p.lens, "cells": p.cells, "tiles": int(info.tiles),
+                      "tile_extent": list(info.tile_extent[:p.k]), "fill_kernel": kernel,
+                      "l2": (f"L2 flushed before each step ({2 * l2_bytes >> 20} MiB write, untimed)" if flush
+                             else "working set > L2 (no flush)"),
+                      "score": score, "score_matches_oracle": checked, "autotune": tuning},
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 3 * steps}
+    plan.close()
+    if args.tile_edge:
+        msadp.msa_config("fill_kernel", 0)
+    return out
+
+
+def run_gb300(args, rank, world, local):
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clocks = ClockSampler(local)
+    main = measure_workload(args.workload, args.steps, args.warmup, args, dist, dev, sms, world, rank, clocks=clocks,
+                            cpu_cells=args.cpu_cells)
+    # every other workload of the benchmark, one GPU: each its own value, roofline and
+    # samples (the clock sampler keeps running through them, all of them GPU-busy)
+    per_workload = None
+    if world == 1 and not args.no_per_workload:
+        per_workload = {}
+        for name in PER_WORKLOADS:
+            if name != args.workload:
+                per_workload[name] = measure_workload(name, max(3, args.steps // 2), args.warmup, args, dist, dev,
+                                                      sms, world, rank)
+    clk = clocks.stop()
+    clk_note = "sampled from the headline timed region through the per-workload measurements" \
+        if per_workload else "sampled during the timed region"
 
     serving = None
     if world == 1 and not args.no_serving:
@@ -523,27 +571,18 @@ def run_gb300(args, rank, world, local):
             except Exception as exc:  # the GPU figures stand without it
                 serving["cpu_baseline"] = {"error": f"{type(exc).__name__}: {exc}"}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        q, dt = time_oracle(p, args.cpu_cells)
-        cpu = {"value": q.cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"oracle on prefixes {q.lens} of {p.name} ({q.cells} cells, {dt:.1f} s)"}
-
     if rank == 0:
+        cfg = dict(main["config"])
+        cfg["parallelism"] = f"replicas{world}"
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": p.name, "k": p.k, "lens": p.lens, "cells": p.cells,
-                       "tiles": int(info.tiles), "fill_kernel": kernel,
-                       "l2": (f"L2 flushed before each step ({2 * l2_bytes >> 20} MiB write, untimed)" if flush
-                              else "working set > L2 (no flush)"), "parallelism": f"replicas{world}",
-                       "score": score, "score_matches_oracle": checked, "autotune": tuning},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": 3 * args.steps, "clocks": clk, "serving": serving,
+            "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": cfg,
+            "roofline": main["roofline"], "cpu_baseline": main["cpu_baseline"], "e2e": main["e2e"],
+            "gpu_launches": main["gpu_launches"],
+            "clocks": (dict(clk, window=clk_note) if clk else clk), "per_workload": per_workload, "serving": serving,
         }
         print(json.dumps(line), flush=True)
-    plan.close()
     if dist:
         dist.destroy_process_group()
     return 0
@@ -559,6 +598,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-per-workload", action="store_true", help="time only the --workload line")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
     ap.add_argument("--tile-edge", type=int, default=0, help="generic tile kernel with this tile edge")
     ap.add_argument("--serve-requests", type=int, default=2000, help="requests of the serving stream")
