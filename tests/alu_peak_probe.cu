@@ -6,11 +6,10 @@
 // Each thread runs NCHAIN accumulators for ITERS iterations; every operation
 // reads two or three different accumulators of the previous iteration (a ring),
 // so the NCHAIN operations of an iteration are independent and no chain can be
-// simplified algebraically; every block times itself with clock64 between two barriers,
-// and the reported figure is
-//     (operations issued by the SM's resident blocks) / (cycles of one block)
-// with BLOCKS_PER_SM equal blocks resident per SM, so it needs no knowledge of
-// the SM clock.
+// simplified algebraically. The grid fills every SM with resident warps; the
+// reported rate is operations / (CUDA-event time x SMs x the maximum SM clock),
+// i.e. lane-operations per SM per clock if the SM ran at its maximum clock
+// (lower clocks lower every figure alike, so ratios between operations hold).
 //
 // Output, one line per operation: name, lane-ops per SM per clock, elapsed ms.
 // "add" (add.s32), "max" (max.s32), "add3" (a + b + c), "max3" (three-input
@@ -24,18 +23,16 @@
 constexpr int NCHAIN = 8;
 constexpr int ITERS = 4096;
 constexpr int THREADS = 512;
-constexpr int BLOCKS_PER_SM = 4;
+constexpr int BLOCKS_PER_SM = 3;  // 3 x 512 threads: the 48 warps an SM holds, all resident at once
 
 template <int OP>
-__global__ void __launch_bounds__(THREADS) probe(int b, int c, int *out, long long *cycles) {
+__global__ void __launch_bounds__(THREADS) probe(int b, int c, int *out) {
     int a[NCHAIN], w[NCHAIN];
 #pragma unroll
     for (int j = 0; j < NCHAIN; ++j) {
         a[j] = threadIdx.x + j;
         w[j] = threadIdx.x * 3 + j;
     }
-    __syncthreads();
-    const long long t0 = clock64();
 #pragma unroll 4
     for (int i = 0; i < ITERS; ++i) {
         // every operation reads two or three different accumulators of the
@@ -66,36 +63,27 @@ __global__ void __launch_bounds__(THREADS) probe(int b, int c, int *out, long lo
             if constexpr (OP == 5) w[j] = m[j];
         }
     }
-    const long long t1 = clock64();
-    __syncthreads();
     int s = 0;
 #pragma unroll
     for (int j = 0; j < NCHAIN; ++j) s += a[j] + w[j];
     out[blockIdx.x * THREADS + threadIdx.x] = s;
-    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
 }
 
 template <int OP>
-static int run(const char *name, int ops_per_step, int sms, int *d_out, long long *d_cyc) {
+static int run(const char *name, int ops_per_step, int sms, double clk_hz, int *d_out) {
     const int blocks = sms * BLOCKS_PER_SM;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    probe<OP><<<blocks, THREADS>>>(3, -5, d_out, d_cyc);  // warm-up
+    probe<OP><<<blocks, THREADS>>>(3, -5, d_out);  // warm-up
     cudaEventRecord(e0);
-    probe<OP><<<blocks, THREADS>>>(3, -5, d_out, d_cyc);
+    probe<OP><<<blocks, THREADS>>>(3, -5, d_out);
     cudaEventRecord(e1);
     if (cudaEventSynchronize(e1) != cudaSuccess) return 1;
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
-    long long *cyc = (long long *)malloc(sizeof(long long) * blocks);
-    cudaMemcpy(cyc, d_cyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost);
-    double mean = 0;
-    for (int i = 0; i < blocks; ++i) mean += (double)cyc[i];
-    mean /= blocks;
-    free(cyc);
-    const double ops_per_block = (double)THREADS * ITERS * NCHAIN * ops_per_step;
-    printf("%s %.1f %.3f\n", name, BLOCKS_PER_SM * ops_per_block / mean, ms);
+    const double ops = (double)blocks * THREADS * ITERS * NCHAIN * ops_per_step;
+    printf("%s %.1f %.3f\n", name, ops / (ms * 1e-3) / sms / clk_hz, ms);
     return 0;
 }
 
@@ -106,17 +94,15 @@ int main() {
     cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, dev);
     printf("sms %d max_clock_khz %d\n", sms, clk);
     int *d_out = nullptr;
-    long long *d_cyc = nullptr;
     if (cudaMalloc(&d_out, sizeof(int) * sms * BLOCKS_PER_SM * THREADS) != cudaSuccess) return 2;
-    if (cudaMalloc(&d_cyc, sizeof(long long) * sms * BLOCKS_PER_SM) != cudaSuccess) return 2;
+    const double hz = clk * 1e3;
     int rc = 0;
-    rc |= run<0>("add", 1, sms, d_out, d_cyc);
-    rc |= run<1>("max", 1, sms, d_out, d_cyc);
-    rc |= run<2>("add3", 2, sms, d_out, d_cyc);
-    rc |= run<3>("max3", 2, sms, d_out, d_cyc);
-    rc |= run<4>("addmax", 2, sms, d_out, d_cyc);
-    rc |= run<5>("relax", 4, sms, d_out, d_cyc);
+    rc |= run<0>("add", 1, sms, hz, d_out);
+    rc |= run<1>("max", 1, sms, hz, d_out);
+    rc |= run<2>("add3", 2, sms, hz, d_out);
+    rc |= run<3>("max3", 2, sms, hz, d_out);
+    rc |= run<4>("addmax", 2, sms, hz, d_out);
+    rc |= run<5>("relax", 4, sms, hz, d_out);
     cudaFree(d_out);
-    cudaFree(d_cyc);
     return rc;
 }
