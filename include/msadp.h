@@ -97,6 +97,10 @@ int msa_set_stream(void *stream);
  *   "fill_kernel"       0: automatic; 1: generic tile kernel; 2: k=3 column kernel;
  *                       3: k=2 band kernel; 4: k=4..6 line kernel
  *   "timing"            1: msa_plan_execute records per-stage CUDA events (default 0)
+ *   "verify_corner"     1: later plans and requests on the k=3 column kernel record the
+ *                       far corner's score during the fill, and the traceback reports
+ *                       MSA_ECUDA when the rescored alignment disagrees with it (about
+ *                       3 % slower); the other fill kernels always do (default 0)
  *   "test_withhold_tile" test hook: the tile with this ticket never publishes its
  *                       completion, so its dependants time out (default -1: off)
  *   "test_poison_tb"    test hook: 1 makes msa_plan_execute fill the plan's traceback

@@ -209,7 +209,7 @@ void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_
     d.lzq = hp.lzq;
     d.tile_base = tile_base;
     d.ntiles = hp.ntiles;
-    d.has_qcorner = hp.kernel == kKernelTiles || hp.kernel == kKernelLines ? 1 : 0;
+    d.has_qcorner = hp.check_corner;
     d.face0_stride = hp.face0_stride;
     d.face1_stride = hp.face1_stride;
     d.face0_rows = hp.face0_rows;
@@ -298,6 +298,8 @@ int msa_config(const char *key, int64_t value) {
         s.timing = value ? 1 : 0;
     } else if (!strcmp(key, "test_withhold_tile")) {
         s.withhold = value;
+    } else if (!strcmp(key, "verify_corner")) {
+        s.verify_corner = value ? 1 : 0;
     } else if (!strcmp(key, "test_poison_tb")) {
         s.poison_tb = value ? 1 : 0;
     } else if (!strcmp(key, "test_shuffle_waves")) {
@@ -336,6 +338,10 @@ int plan_create(int k, const int32_t *lens, const char *alphabet, int kernel_cho
     if (rc) {
         delete p;
         return set_error(rc, "%s", err.c_str());
+    }
+    {
+        std::lock_guard<std::mutex> g(settings_mutex());
+        p->hp.check_corner = p->hp.kernel != kKernelCol3 || settings().verify_corner ? 1 : 0;
     }
     strncpy(p->alphabet, alphabet, MSA_MAX_ALPHABET);
     p->ws_bytes = plan_layout(p->hp, nullptr, nullptr, &p->reset_bytes);
@@ -413,6 +419,7 @@ int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_su
     L.withhold = withhold;
     L.nprob = 1;
     L.tab_ints = plan->hp.A * (plan->hp.A + 1) * 32;  // table plus the sentinel column
+    L.corner = plan->hp.check_corner;
     if (plan->hp.kernel == kKernelCol3) {
         if (plan->epoch >= 32767) {  // tags (epoch << 16) + T would wrap: start over from cleared faces
             e = clear_faces(plan->hp, plan->pp, s);

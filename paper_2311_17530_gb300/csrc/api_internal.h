@@ -20,6 +20,7 @@ struct Settings {
     int64_t withhold = -1;
     int64_t timing = 0;
     int64_t poison_tb = 0;
+    int64_t verify_corner = 0;
 };
 
 // Header of a workspace; zeroed before every execution.

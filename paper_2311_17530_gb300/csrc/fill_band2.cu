@@ -18,7 +18,8 @@
 // W(x) = x0 + 2 x1, single-sequence moves cost 0 and the diagonal move the
 // pair table entry ((sub - 2 gap) << 2); one max gives the best value and, in its
 // low two bits, the lowest move mask among ties. Traceback bytes are written
-// row-major, four columns per 4-byte store.
+// row-major, four columns per 4-byte store; the lane that computes the far corner
+// records its key, which the traceback compares with the rescored path.
 #include "api_internal.h"
 #include "device_common.cuh"
 
@@ -115,6 +116,8 @@ __global__ void __launch_bounds__(kBandWarps * 32) fill_band2_kernel(const Launc
                 if ((j & 3) == 3 || j == rho1 - 1) {
                     *reinterpret_cast<uint32_t *>(tbrow + (j & ~3)) = pk;
                     pk = 0;
+                    // the far corner's key, for the traceback's cross-check
+                    if (j == rho1 - 1 && i == rho0 - 1) *P.qcorner = Vn;
                 }
                 if (lane == 31) {
                     face_out[j] = Vn;

@@ -145,6 +145,9 @@ struct C3Ln {
     int tagout;         // tag base of ring-out entries (0: shared ring, epoch << 16: global face)
     int tagf1;          // tag base of this column's F1 entries
     bool last;          // lane 31 writes the F1 face
+    int ctime;          // CTA time at which this lane computes the far corner (else never)
+    int crow;           // the corner's row among this lane's R rows
+    int32_t *qcorner;   // where the corner's key goes (for the traceback's cross-check)
 };
 
 // Per-block addresses (block = U steps starting at CTA time T0).
@@ -227,6 +230,19 @@ __device__ __forceinline__ void c3_step(C3St &g, const C3Ln &c, const char *tab,
         g.P[r] = pn;
     }
     g.VM = VMn;
+}
+
+// A step of the block that holds the far corner's CTA time (kernels that record
+// the corner): the plain step, then the corner's lane stores its row's key.
+template <int s>
+__device__ __forceinline__ void c3_capture_step(C3St &g, const C3Ln &c, const char *tab, const C3Blk &b, int T0,
+                                                int lane, C3Smem &sm, const LaunchDesc &L) {
+    c3_step<s>(g, c, tab, b, T0, lane, sm, L);
+    if (T0 + s == c.ctime) {
+        // a select chain (R is 2 or 4): a loop over r would index the registers dynamically
+        const int v = c.crow == 0 ? g.V[0] : c.crow == 1 ? g.V[1] : c.crow == 2 ? g.V[2 % c3::R] : g.V[c3::R - 1];
+        __stcg(c.qcorner, v);
+    }
 }
 
 struct C3Col {
@@ -393,6 +409,10 @@ __device__ __forceinline__ bool c3_block_wait(C3Smem &sm, int w, int T0, const L
 
 }  // namespace
 
+// CAP: the warp that computes the far corner records its key for the traceback's
+// cross-check; the block holding it runs a capturing copy of the steps (which
+// costs registers, so plain launches use the kernel without it).
+template <bool CAP>
 __global__ void __launch_bounds__(c3::THREADS, 1) fill_col3_kernel(const LaunchDesc L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C3Smem &sm = *reinterpret_cast<C3Smem *>(smem_raw);
@@ -485,6 +505,13 @@ __global__ void __launch_bounds__(c3::THREADS, 1) fill_col3_kernel(const LaunchD
             }
             c.laneb = (code1 * (A + 1) * 32 + lane) * 4;
             c.Wl = cc.A * c3::WR + 64 * cc.B - 2 * lane - 3 * c.wR;
+            {  // the far corner (len0, len1, len2): row rho of lane l at CTA time len2 + l + rho
+                const int rhoc = P.len[0] - cc.A * c3::WR, lc = P.len[1] - 32 * cc.B;
+                const bool mine = rhoc >= c.wR && rhoc < c.wR + c3::R && lc == lane;
+                c.ctime = mine ? P.len[2] + lc + rhoc : (int)0x80000000;
+                c.crow = rhoc - c.wR;
+                c.qcorner = P.qcorner;
+            }
             const char *tab = reinterpret_cast<const char *>(tabr);
             const uint16_t *c2lane = c2off + c3::CODEPAD + 2 - lane - c.wR;  // x2 = T + 2 - lane - wR at T
 
@@ -508,6 +535,12 @@ __global__ void __launch_bounds__(c3::THREADS, 1) fill_col3_kernel(const LaunchD
 
             unsigned long long *ringout = lastw ? cc.f0dst + lane : &sm.ring[w + 1][0][lane];
             unsigned char *tbw = P.tb + (int64_t)lin * c3::tb_col_bytes(P.rho[2]) + (w * 32 + lane) * c3::R;
+            // the block of the corner's CTA time, the same in every lane of its warp
+            int T0c = -2 * c3::U;
+            if (CAP) {
+                const int ct = __shfl_sync(kFull, c.ctime, (P.len[1] - 32 * cc.B) & 31);
+                if (ct != (int)0x80000000) T0c = ct / c3::U * c3::U;
+            }
             for (int T0 = -c3::U; T0 < cc.N; T0 += c3::U) {
                 if (!c3_block_wait(sm, w, T0, L)) break;
                 if (T0 == 0 && origin) g.P[0] = 0;  // H(0) = 0, no move
@@ -518,14 +551,25 @@ __global__ void __launch_bounds__(c3::THREADS, 1) fill_col3_kernel(const LaunchD
                 b.tbp = tbw + (int64_t)(T0 + c3::U) * (c3::W * 32 * c3::R);
                 b.f1o = cc.f1dst + (int64_t)(T0 + c3::U) * c3::WR + c.wR;
                 b.c2p = c2lane + T0;
-                c3_step<0>(g, c, tab, b, T0, lane, sm, L);
-                c3_step<1>(g, c, tab, b, T0, lane, sm, L);
-                c3_step<2>(g, c, tab, b, T0, lane, sm, L);
-                c3_step<3>(g, c, tab, b, T0, lane, sm, L);
-                c3_step<4>(g, c, tab, b, T0, lane, sm, L);
-                c3_step<5>(g, c, tab, b, T0, lane, sm, L);
-                c3_step<6>(g, c, tab, b, T0, lane, sm, L);
-                c3_step<7>(g, c, tab, b, T0, lane, sm, L);
+                if (!CAP || T0 != T0c) {
+                    c3_step<0>(g, c, tab, b, T0, lane, sm, L);
+                    c3_step<1>(g, c, tab, b, T0, lane, sm, L);
+                    c3_step<2>(g, c, tab, b, T0, lane, sm, L);
+                    c3_step<3>(g, c, tab, b, T0, lane, sm, L);
+                    c3_step<4>(g, c, tab, b, T0, lane, sm, L);
+                    c3_step<5>(g, c, tab, b, T0, lane, sm, L);
+                    c3_step<6>(g, c, tab, b, T0, lane, sm, L);
+                    c3_step<7>(g, c, tab, b, T0, lane, sm, L);
+                } else {
+                    c3_capture_step<0>(g, c, tab, b, T0, lane, sm, L);
+                    c3_capture_step<1>(g, c, tab, b, T0, lane, sm, L);
+                    c3_capture_step<2>(g, c, tab, b, T0, lane, sm, L);
+                    c3_capture_step<3>(g, c, tab, b, T0, lane, sm, L);
+                    c3_capture_step<4>(g, c, tab, b, T0, lane, sm, L);
+                    c3_capture_step<5>(g, c, tab, b, T0, lane, sm, L);
+                    c3_capture_step<6>(g, c, tab, b, T0, lane, sm, L);
+                    c3_capture_step<7>(g, c, tab, b, T0, lane, sm, L);
+                }
             }
             __syncwarp();
             if (lane == 0) st_release_shared(&sm.prog[w], 1 << 30);
@@ -546,15 +590,19 @@ int col3_smem_bytes(int alphabet_size) {
 cudaError_t col3_attributes() {
     static DeviceOnce once;
     return once.run([] {
-        return cudaFuncSetAttribute(fill_col3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    col3_smem_bytes(c3::MAXA));
+        cudaError_t e = cudaFuncSetAttribute(fill_col3_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             col3_smem_bytes(c3::MAXA));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(fill_col3_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     col3_smem_bytes(c3::MAXA));
+        return e;
     });
 }
 
 int fill_col3_ctas_per_sm(int smem) {
     if (col3_attributes() != cudaSuccess) return 0;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fill_col3_kernel, c3::THREADS, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fill_col3_kernel<false>, c3::THREADS, smem) != cudaSuccess)
         return 0;
     return n;
 }
@@ -563,7 +611,10 @@ cudaError_t launch_fill_col3(const LaunchDesc &L, int grid, int smem, cudaStream
     cudaError_t e = col3_attributes();
     if (e != cudaSuccess) return e;
     if (smem > col3_smem_bytes(c3::MAXA)) return cudaErrorInvalidValue;
-    fill_col3_kernel<<<grid, c3::THREADS, smem, s>>>(L);
+    if (L.corner)
+        fill_col3_kernel<true><<<grid, c3::THREADS, smem, s>>>(L);
+    else
+        fill_col3_kernel<false><<<grid, c3::THREADS, smem, s>>>(L);
     return cudaGetLastError();
 }
 

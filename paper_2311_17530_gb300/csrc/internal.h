@@ -92,7 +92,7 @@ struct LaunchDesc {
     int32_t nprob;
     int32_t tab_ints;        // column kernel: shared-memory ints of the replicated table
     int32_t epoch;           // column kernel: tag of this launch's face entries (>= 1)
-    int32_t pad2;
+    int32_t corner;          // column kernel: record the far corner's key (the traceback checks it)
 };
 
 // Tile shapes of the generic kernel. A shape is named by its edge E: the tile

@@ -40,6 +40,8 @@ struct HostPlan {
     int32_t lzq = 0;                   // line kernel: words per line in a tile's face block
     int32_t edge = 0;              // tile edge of the generic kernel (tile_ext); longest segment of the
                                    // line kernel; 0 for the column and band kernels
+    int32_t check_corner = 1;      // the fill records the far corner's key and the traceback checks it
+                                   // (always, but optional for the column kernel: msa_config "verify_corner")
     int32_t pair_min_sum = 0;
     int32_t w_corner = 0;
     int32_t len_sum = 0;

@@ -219,6 +219,7 @@ int Server::submit(const msa_request *req, uint64_t *out) {
         delete r;
         return set_error(rc, "%s", err.c_str());
     }
+    r->hp.check_corner = r->hp.kernel != kKernelCol3 || cfg.verify_corner ? 1 : 0;
     size_t rb = 0;
     r->ws_bytes = plan_layout(r->hp, nullptr, nullptr, &rb);
     const size_t budget = (size_t)cfg.budget_mb << 20;
@@ -565,6 +566,7 @@ int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg
         L.nprob = g.count;
         L.tab_ints = g.maxA * (g.maxA + 1) * 32;
         L.epoch = epoch_;
+        for (int j = 0; j < g.count; ++j) L.corner |= batch[g.first + j]->hp.check_corner;
         e = g.kernel == kKernelCol3    ? launch_fill_col3(L, g.grid, col3_smem_bytes(g.maxA), s)
           : g.kernel == kKernelBand2 ? launch_fill_band2(L, g.grid, s)
           : g.kernel == kKernelLines ? launch_fill_lines(g.k, g.edge, L, g.grid, s)

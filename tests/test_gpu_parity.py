@@ -225,3 +225,49 @@ def test_k3_auto_picks_column_kernel():
     p = inputs.k3_protein()
     with msa.Plan(3, [10, 10, 10], p.alphabet) as plan:
         assert plan.info().fill_kernel == 2
+
+
+@pytest.mark.parametrize("kernel,k,lens", [(2, 3, [40, 37, 45]), (2, 3, [63, 95, 70]), (3, 2, [150, 170]),
+                                           (3, 2, [33, 400]), (4, 4, [9, 13, 10, 40]), (1, 4, [9, 13, 10, 40])])
+def test_every_fill_kernel_records_the_corner_key(kernel, k, lens):
+    """Every fill kernel records the far corner's packed key; the traceback
+    compares the rescored path with it. A consistent result (status 0, the
+    oracle's score) shows the record and the check agree for each kernel."""
+    msa.msa_config("fill_kernel", kernel)
+    msa.msa_config("verify_corner", 1)  # the column kernel records it only when asked
+    try:
+        p = inputs.random_problem(6100 + sum(lens), k, lens, alphabet=inputs.PROTEIN, related=True)
+        with msa.Plan(k, p.lens, p.alphabet) as plan:
+            assert plan.info().fill_kernel == kernel
+        o = oracle.align_problem(p)
+        score, rows, status, _ = run_plan(p)
+        assert status == 0 and (score, rows) == (o.score, o.rows)
+    finally:
+        msa.msa_config("verify_corner", 0)
+        msa.msa_config("fill_kernel", 0)
+
+
+@pytest.mark.parametrize("seed", [3, 99])
+@pytest.mark.parametrize("kernel,k,lens", [(2, 3, [70, 65, 90]), (3, 2, [150, 170]), (1, 3, [30, 25, 28]),
+                                           (1, 4, [9, 8, 10, 7]), (1, 5, [5, 4, 6, 5, 4])])
+def test_shuffled_orders_over_a_poisoned_traceback(kernel, k, lens, seed):
+    """Tickets permuted inside every wave (another topological order of the same
+    tiles or columns) and the traceback tensor filled with 0xFF before the fill:
+    every cell must still equal the oracle (a missed dependency or an unwritten
+    cell would show), and no cell may keep 0xFF (no move for k < 8)."""
+    msa.msa_config("fill_kernel", kernel)
+    msa.msa_config("test_shuffle_waves", seed)
+    msa.msa_config("test_poison_tb", 1)
+    try:
+        p = inputs.random_problem(6200 + seed + 10 * kernel + k, k, lens, alphabet=inputs.PROTEIN, related=True)
+        with msa.Plan(k, p.lens, p.alphabet) as plan:
+            assert plan.info().fill_kernel == kernel
+        o = oracle.align_problem(p, want_tb=True)
+        score, rows, status, tb = run_plan(p, want_tb=True)
+        assert status == 0 and (score, rows) == (o.score, o.rows)
+        assert not (tb == 0xFF).any()
+        np.testing.assert_array_equal(tb, o.tb)
+    finally:
+        msa.msa_config("test_poison_tb", 0)
+        msa.msa_config("test_shuffle_waves", 0)
+        msa.msa_config("fill_kernel", 0)
