@@ -203,7 +203,9 @@ int msa_plan_timings(msa_plan *plan, float out_ms[3]);
  * while another allocator owns the GPU's memory, latency-critical loops where an
  * allocation would stall, callers that cannot recover from an allocation failure
  * mid-request. Inputs, outputs and asynchrony are those of msa_plan_execute
- * (d_residues, d_subst, d_result, d_masks are the caller's device buffers); all
+ * (d_residues, d_subst, d_result, d_masks are the caller's device buffers; the
+ * call only enqueues work on the stream and reads no host memory after it
+ * returns); all
  * working memory is a fixed array of MSA_NOALLOC_SCRATCH_BYTES compiled into the
  * library, held by every GPU that loads it until the process exits. Problems
  * whose working set exceeds it (about 6 million cells) return MSA_ETOOBIG with

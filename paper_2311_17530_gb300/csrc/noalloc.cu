@@ -68,44 +68,34 @@ __global__ void noalloc_order_kernel(const ProblemDesc *prob, uint64_t *order, i
     }
 }
 
-// Shape, strides and tile grid of the generic tile kernel, computed without
-// heap memory (the order itself is built on the device).
+// The 256-entry character -> code map, passed by value to the set-up kernel.
+struct AmapBytes {
+    uint8_t m[256];
+};
+
+// Writes the problem descriptor and the character map into the scratch. Both
+// travel as kernel parameters, so no host memory is read after the call returns
+// (no copy from pageable memory, which would block and could not be captured).
+__global__ void noalloc_setup_kernel(const ProblemDesc d, const AmapBytes a, ProblemDesc *prob, uint8_t *amap) {
+    if (threadIdx.x == 0) *prob = d;
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) amap[i] = a.m[i];
+}
+
+// Shape, strides and tile grid of the generic tile kernel: the planner's own
+// plan_shape (the same limits and layouts as every plan), which needs no heap
+// memory; the ticket order is built on the device instead.
 int noalloc_plan(int k, const int32_t *lens, int A, HostPlan &hp) {
-    hp.k = k;
-    hp.A = A;
-    hp.kernel = kKernelTiles;
     long double cells = 1;
-    int64_t len_sum = 0, w_corner = 0, pair_min = 0;
     for (int i = 0; i < k; ++i) {
         if (lens[i] < 0) return set_error(MSA_EINVAL, "lens[%d]=%d is negative", i, lens[i]);
-        hp.lens[i] = lens[i];
-        hp.rho[i] = lens[i] + 1;
-        cells *= (long double)hp.rho[i];
-        len_sum += lens[i];
-        w_corner += (int64_t)lens[i] << i;
-        for (int j = i + 1; j < k; ++j) pair_min += lens[i] < lens[j] ? lens[i] : lens[j];
+        cells *= (long double)lens[i] + 1;
     }
-    if (cells > (long double)MSA_NOALLOC_SCRATCH_BYTES || len_sum >= (1 << 24) || w_corner >= (1 << 28))
-        return set_error(MSA_ETOOBIG, "msa_align_noalloc: %.3Lg cells exceed the %u-byte static scratch",
-                         cells, (unsigned)MSA_NOALLOC_SCRATCH_BYTES);
-    hp.cells = (int64_t)cells;
-    hp.len_sum = (int32_t)len_sum;
-    hp.w_corner = (int32_t)w_corner;
-    hp.pair_min_sum = (int32_t)pair_min;
-    hp.edge = tile_edge_for(k);
-    tile_extents(k, lens, kKernelTiles, hp.edge, hp.E);
-    int64_t nt = 1;
-    int gsum = 0;
-    for (int i = k - 1; i >= 0; --i) {
-        hp.G[i] = (hp.rho[i] + hp.E[i] - 1) / hp.E[i];
-        hp.gstride[i] = nt;
-        nt *= hp.G[i];
-        gsum += hp.G[i];
-    }
-    hp.ntiles = nt;
-    hp.waves = gsum - k + 1;
-    if (!score_and_traceback_layout(hp))
-        return set_error(MSA_ETOOBIG, "msa_align_noalloc: score scratch beyond 32-bit offsets");
+    if (cells > (long double)MSA_NOALLOC_SCRATCH_BYTES)
+        return set_error(MSA_ETOOBIG, "msa_align_noalloc: %.3Lg cells exceed the %u-byte static scratch", cells,
+                         (unsigned)MSA_NOALLOC_SCRATCH_BYTES);
+    std::string err;
+    const int rc = plan_shape(k, lens, A, kKernelTiles, hp, err, tile_edge_for(k));
+    if (rc) return set_error(rc, "msa_align_noalloc: %s", err.c_str());
     return MSA_OK;
 }
 
@@ -165,12 +155,16 @@ extern "C" int msa_align_noalloc(int k, const int32_t *lens, const char *alphabe
         std::lock_guard<std::mutex> g(settings_mutex());
         spin_ms = settings().spin_ms;
     }
-    // zero what the previous call left behind: launch state, tile flags, wave counters
+    // zero what the previous call left behind (launch state, tile flags, wave
+    // counters), then the descriptor and character map by value
     e = cudaMemsetAsync(base, 0, reset_bytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(wave_cnt, 0, (size_t)hp.waves * 4, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(pp.prob, &d, sizeof d, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(pp.amap, amap, 256, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_error(e, "static scratch set-up");
+    AmapBytes am;
+    memcpy(am.m, amap, 256);
+    noalloc_setup_kernel<<<1, 256, 0, s>>>(d, am, pp.prob, pp.amap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(e, "set-up kernel launch");
     noalloc_order_kernel<<<1, 1024, 0, s>>>(pp.prob, pp.order, wave_cnt, hp.waves);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(e, "order kernel launch");

@@ -210,7 +210,7 @@ bool score_and_traceback_layout(HostPlan &hp) {
     return true;
 }
 
-int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err, int edge) {
+int plan_shape(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err, int edge) {
     char buf[256];
     if (k < 2 || k > MSA_MAX_K) {
         snprintf(buf, sizeof buf, "k=%d outside [2,%d]", k, MSA_MAX_K);
@@ -297,10 +297,7 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
         hp.qelems = hp.ntiles * hp.face0_stride;
     }
 
-    if (hp.kernel == kKernelCol3) {
-        // faces between columns and the column order: a column (a, b) can start
-        // about a*(WR + U) + b*(32 + U) CTA-time steps after the first, so tickets
-        // follow that estimate (every producer gets a smaller ticket)
+    if (hp.kernel == kKernelCol3) {  // faces between columns
         const int rho2 = hp.rho[2];
         hp.face0_rows = c3::face0_rows(rho2);
         hp.face1_rows = c3::face1_rows(rho2);
@@ -310,6 +307,18 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
         hp.aux_elems = nt * hp.face1_stride;
         hp.tb_layout = 1;
         hp.tb_dev_bytes = nt * c3::tb_col_bytes(rho2);
+    }
+    return MSA_OK;
+}
+
+int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err, int edge) {
+    const int rc = plan_shape(k, lens, A, kernel_choice, hp, err, edge);
+    if (rc) return rc;
+    const int64_t nt = hp.ntiles;
+    if (hp.kernel == kKernelCol3) {
+        // the column order: a column (a, b) can start about a*(WR + U) + b*(32 + U)
+        // CTA-time steps after the first, so tickets follow that estimate (every
+        // producer gets a smaller ticket)
         std::vector<std::pair<int64_t, int64_t>> key(nt);
         for (int64_t t = 0; t < nt; ++t) {
             const int64_t a = t / hp.G[1], b = t % hp.G[1];

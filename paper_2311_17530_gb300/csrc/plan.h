@@ -74,8 +74,13 @@ void set_prefer_tiles_lines(int k, bool v);
 // False when the scratch would need offsets beyond 32 bits.
 bool score_and_traceback_layout(HostPlan &hp);
 
-// Fill `hp` for one problem. Returns MSA_OK or an MSA_E* code with `err` set.
-// edge < 0 takes the current tuned edge for k.
+// Shape, limits, tile grid and layouts of one problem without the ticket order:
+// everything of make_plan that needs no heap memory. Returns MSA_OK or an MSA_E*
+// code with `err` set; edge < 0 takes the current tuned edge for k.
+int plan_shape(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err, int edge = -1);
+
+// Fill `hp` for one problem: plan_shape and the ticket order. Returns MSA_OK or
+// an MSA_E* code with `err` set. edge < 0 takes the current tuned edge for k.
 int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err,
               int edge = -1);
 
