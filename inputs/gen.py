@@ -175,6 +175,23 @@ def k6_protein(seed: int = 4, table_seed: int = 2) -> Problem:
     return Problem("k6_protein_18_24", seqs, PROTEIN, table, -6, seed)
 
 
+def k4_dna_profile(seed: int = 3) -> Problem:
+    """k=4 DNA at a size for full counter captures (lengths 70/70/70/100, 36M cells;
+    the fill's faces and traceback bytes still exceed the L2), same recipe as k4_dna."""
+    rng = np.random.default_rng(seed)
+    seqs = related_family(rng, DNA, [70, 70, 70, 100], 0.15, 0.05)
+    return Problem("k4_dna_profile_70_70_70_100", seqs, DNA, dna_table(), -8, seed)
+
+
+def k6_protein_profile(seed: int = 4, table_seed: int = 2) -> Problem:
+    """k=6 protein at a size for full counter captures (six lengths of 17, 34M cells),
+    same recipe and table as k6_protein."""
+    table = protein_table(np.random.default_rng(table_seed))
+    rng = np.random.default_rng(seed)
+    seqs = related_family(rng, PROTEIN, [17] * 6, 0.25, 0.05)
+    return Problem("k6_protein_profile_17", seqs, PROTEIN, table, -6, seed)
+
+
 def k2_protein(seed: int = 6, table_seed: int = 2) -> Problem:
     """k=2 protein pair, lengths 5000/4800 from one ancestor (sub 0.2, indel 0.05).
 
@@ -193,6 +210,9 @@ WORKLOADS = {
     "k3_protein": k3_protein,
     "k4_dna": k4_dna,
     "k6_protein": k6_protein,
+    # smaller cases of the same recipes, for full counter captures
+    "k4_dna_profile": k4_dna_profile,
+    "k6_protein_profile": k6_protein_profile,
 }
 
 SERVING_LEN_RANGE = {2: (200, 2000), 3: (40, 300), 4: (20, 80)}
