@@ -154,6 +154,9 @@ KERNEL_SOURCES = {
                    "csrc/device_common.cuh", "../include/msadp.h"],
     "fill_lines": ["csrc/fill_lines.cuh"] + [f"csrc/fill_lines_k{k}.cu" for k in range(4, 7)] +
                   ["csrc/internal.h", "csrc/device_common.cuh", "../include/msadp.h"],
+    "fill_lines_stream": ["csrc/fill_lines_stream.cuh", "csrc/fill_lines.cuh"] +
+                         [f"csrc/fill_stream_k{k}.cu" for k in range(4, 6)] +
+                         ["csrc/internal.h", "csrc/device_common.cuh", "../include/msadp.h"],
 }
 
 
@@ -508,7 +511,8 @@ def measure_workload(name, steps, warmup, args, dist, dev, sms, world, rank, clo
                "h2d_bytes_per_step": total_len + p.subst.size * 4,
                "d2h_bytes_per_step": 16 + total_len, "ms_per_step": 1e3 * tot / steps}
 
-    kernel = {1: "fill_tiles", 2: "fill_col3", 3: "fill_band2", 4: "fill_lines"}[int(info.fill_kernel)]
+    kernel = {1: "fill_tiles", 2: "fill_col3", 3: "fill_band2", 4: "fill_lines",
+              5: "fill_lines_stream"}[int(info.fill_kernel)]
     ops = alg_ops_per_cell(p.k) * p.cells
     achieved = ops / (fill_ms / 1e3) / 1e12
     peak = alu_peak_tiops(sms)

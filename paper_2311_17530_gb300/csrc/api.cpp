@@ -119,7 +119,7 @@ int device_sm_count() {
 int persistent_grid(int k, int kernel, int64_t units, int A, int edge) {
     // resident CTAs per SM, cached per (kernel, k, alphabet size or tile edge)
     static std::mutex mu;
-    static int cache[5][MSA_MAX_K + 1][MSA_MAX_ALPHABET + 1] = {};
+    static int cache[kKernelCount][MSA_MAX_K + 1][MSA_MAX_ALPHABET + 1] = {};
     int c;
     {
         std::lock_guard<std::mutex> g(mu);
@@ -131,15 +131,18 @@ int persistent_grid(int k, int kernel, int64_t units, int A, int edge) {
             slot = kernel == kKernelCol3    ? fill_col3_ctas_per_sm(col3_smem_bytes(A))
                    : kernel == kKernelBand2 ? fill_band2_ctas_per_sm()
                    : kernel == kKernelLines ? fill_lines_ctas_per_sm(k, edge)
+                   : kernel == kKernelStream ? fill_stream_ctas_per_sm(k)
                                             : fill_tiles_ctas_per_sm(k, edge);
             if (slot <= 0) slot = 1;
         }
         c = slot;
     }
-    // the tile, line and band kernels take one unit per warp, the column kernel one per CTA
+    // the tile, line and band kernels take one unit per warp, the column kernel
+    // and the streamed line kernel one per CTA
     const int per_cta = kernel == kKernelCol3    ? 1
                       : kernel == kKernelBand2 ? fill_band2_warps_per_cta()
                       : kernel == kKernelLines ? std::max(1, fill_lines_warps_per_cta(k, edge))
+                      : kernel == kKernelStream ? 1
                                                : std::max(1, fill_tiles_warps_per_cta(k, edge));
     int64_t need = (units + per_cta - 1) / per_cta;
     int64_t g = (int64_t)c * device_sm_count();
@@ -201,6 +204,7 @@ void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_
         d.G[i] = hp.G[i];
         d.E[i] = hp.E[i];
         d.gstride[i] = hp.gstride[i];
+        d.sgstride[i] = hp.sgstride[i];
         d.qstride[i] = hp.qstride[i];
         d.tbstride[i] = hp.tbstride[i];
         d.lst[i] = hp.lst[i];
@@ -239,6 +243,7 @@ int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t 
     cudaError_t e = hp.kernel == kKernelCol3    ? launch_fill_col3(L, grid, col3_smem_bytes(hp.A), s)
                   : hp.kernel == kKernelBand2 ? launch_fill_band2(L, grid, s)
                   : hp.kernel == kKernelLines ? launch_fill_lines(hp.k, hp.edge, L, grid, s)
+                  : hp.kernel == kKernelStream ? launch_fill_stream(hp.k, L, grid, s)
                                               : launch_fill_tiles(hp.k, hp.edge, L, grid, s);
     return e == cudaSuccess ? MSA_OK : cuda_error(e, "fill kernel launch");
 }
@@ -254,7 +259,7 @@ struct msa_plan {
     PlanPointers pp;
     int grid = 1;
     cudaStream_t last_stream = nullptr;
-    int32_t epoch = 0;  // tag of the last execution's face entries (column kernel)
+    int32_t epoch = 0;  // tag of the last execution's face entries (column and streamed line kernels)
     // per-stage events of timed executions, a ring of kTimedRing executions
     static constexpr int kTimedRing = 256;
     std::vector<cudaEvent_t> ev;
@@ -292,7 +297,7 @@ int msa_config(const char *key, int64_t value) {
     } else if (!strcmp(key, "batching")) {
         s.batching = value ? 1 : 0;
     } else if (!strcmp(key, "fill_kernel")) {
-        if (value < 0 || value > 4) return set_error(MSA_EINVAL, "fill_kernel must be 0, 1, 2, 3 or 4");
+        if (value < 0 || value > 5) return set_error(MSA_EINVAL, "fill_kernel must be 0, 1, 2, 3, 4 or 5");
         s.fill_kernel = value;
     } else if (!strcmp(key, "timing")) {
         s.timing = value ? 1 : 0;
@@ -361,14 +366,14 @@ int plan_create(int k, const int32_t *lens, const char *alphabet, int kernel_cho
     if (e == cudaSuccess)
         e = cudaMemcpy(p->pp.order, p->hp.order.data(), p->hp.order.size() * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->pp.amap, amap, 256, cudaMemcpyHostToDevice);
-    // column kernel faces start with tag 0, which no execution uses
-    if (e == cudaSuccess && p->hp.kernel == kKernelCol3) e = clear_faces(p->hp, p->pp);
+    // tagged faces start with tag 0, which no execution uses
+    if (e == cudaSuccess && tagged_faces(p->hp.kernel)) e = clear_faces(p->hp, p->pp);
     if (e != cudaSuccess) {
         cudaFree(p->ws);
         delete p;
         return cuda_error(e, "plan upload");
     }
-    p->grid = persistent_grid(k, p->hp.kernel, p->hp.ntiles, A, p->hp.edge);
+    p->grid = persistent_grid(k, p->hp.kernel, p->hp.nunits, A, p->hp.edge);
     *out_plan = p;
     return MSA_OK;
 }
@@ -411,7 +416,7 @@ int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_su
     memset(&L, 0, sizeof L);
     L.probs = plan->pp.prob;
     L.order = plan->pp.order;
-    L.ntickets = plan->hp.ntiles;
+    L.ntickets = plan->hp.nunits;
     L.done = plan->pp.done;
     L.ticket = &plan->pp.state->ticket;
     L.err = &plan->pp.state->err;
@@ -420,8 +425,8 @@ int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_su
     L.nprob = 1;
     L.tab_ints = plan->hp.A * (plan->hp.A + 1) * 32;  // table plus the sentinel column
     L.corner = plan->hp.check_corner;
-    if (plan->hp.kernel == kKernelCol3) {
-        if (plan->epoch >= 32767) {  // tags (epoch << 16) + T would wrap: start over from cleared faces
+    if (tagged_faces(plan->hp.kernel)) {
+        if (plan->epoch >= 32767) {  // column kernel tags (epoch << 16) + T would wrap: start over from cleared faces
             e = clear_faces(plan->hp, plan->pp, s);
             if (e != cudaSuccess) return cuda_error(e, "face reset");
             plan->epoch = 0;

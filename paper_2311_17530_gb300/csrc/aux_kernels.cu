@@ -13,6 +13,17 @@ __global__ void encode_kernel(const ProblemDesc *probs, const IODesc *io_arr, IO
     const ProblemDesc &P = probs[p];
     const IODesc io = io_arr ? io_arr[p] : io1;
     msa_device_result *st = P.istat;
+    if (P.clear_faces) {
+        // Column-kernel faces in a reused region: tag 0 everywhere, so that no
+        // stale word can pass for an entry of this launch (the fill runs after this
+        // kernel on the same stream). Face sizes are multiples of 64 ints.
+        const int64_t n0 = P.face0_stride * P.ntiles / 4, n1 = P.face1_stride * P.ntiles / 4;
+        const int4 z = make_int4(0, 0, 0, 0);
+        for (int64_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n0; i += (int64_t)gridDim.x * blockDim.x)
+            reinterpret_cast<int4 *>(P.Q)[i] = z;
+        for (int64_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += (int64_t)gridDim.x * blockDim.x)
+            reinterpret_cast<int4 *>(P.aux)[i] = z;
+    }
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.ncode; i += gridDim.x * blockDim.x) {
         const uint8_t c = P.amap[(uint8_t)io.residues[i]];
         if (c == 0xFF) atomicCAS(&st->status, 0, MSA_EINVAL);
@@ -63,8 +74,9 @@ __global__ void encode_kernel(const ProblemDesc *probs, const IODesc *io_arr, IO
 }
 
 cudaError_t launch_encode(const ProblemDesc *d_probs, int nprob, int max_ncode,
-                          const IODesc *io_array, IODesc io_single, cudaStream_t s) {
+                          const IODesc *io_array, IODesc io_single, cudaStream_t s, int min_blocks) {
     int bx = (max_ncode + 255) / 256;
+    if (bx < min_blocks) bx = min_blocks;
     if (bx < 1) bx = 1;
     if (bx > 64) bx = 64;
     encode_kernel<<<dim3(bx, nprob), 256, 0, s>>>(d_probs, io_array, io_single);
@@ -159,6 +171,17 @@ int fill_lines_warps_per_cta(int k, int z) {
     }
 }
 
+cudaError_t launch_fill_stream_k4(const LaunchDesc &L, int grid, cudaStream_t s);
+cudaError_t launch_fill_stream_k5(const LaunchDesc &L, int grid, cudaStream_t s);
+int fill_stream_ctas_k4();
+int fill_stream_ctas_k5();
+
+cudaError_t launch_fill_stream(int k, const LaunchDesc &L, int grid, cudaStream_t s) {
+    return k == 4 ? launch_fill_stream_k4(L, grid, s) : k == 5 ? launch_fill_stream_k5(L, grid, s) : cudaErrorInvalidValue;
+}
+
+int fill_stream_ctas_per_sm(int k) { return k == 4 ? fill_stream_ctas_k4() : k == 5 ? fill_stream_ctas_k5() : 0; }
+
 cudaError_t col3_attributes();
 
 // Every kernel attribute the launch wrappers need on the current device, so that
@@ -174,6 +197,8 @@ cudaError_t prepare_kernel_attributes() {
         for (int i = 0; i < kMaxLineSegments && e == cudaSuccess; ++i)
             if (line_z_candidate(k, i) > 0 && fill_lines_ctas_per_sm(k, line_z_candidate(k, i)) <= 0)
                 e = cudaErrorInvalidValue;
+    for (int k = kStreamMinK; k <= kStreamMaxK && e == cudaSuccess; ++k)
+        if (fill_stream_ctas_per_sm(k) <= 0) e = cudaErrorInvalidValue;
     return e;
 }
 

@@ -40,6 +40,7 @@ struct ProblemDesc {
     int32_t G[MSA_MAX_K];        // tile grid
     int32_t E[MSA_MAX_K];        // tile extents used by the kernel
     int64_t gstride[MSA_MAX_K];  // tile-grid row-major strides
+    int64_t sgstride[MSA_MAX_K]; // streamed line kernel: strides of the grid of super-blocks (its tickets)
     int64_t qstride[MSA_MAX_K];  // score scratch strides (int32 elements)
     int64_t tbstride[MSA_MAX_K]; // traceback tensor strides (bytes)
     int64_t tile_base;           // first index of this problem in done[]
@@ -48,7 +49,7 @@ struct ProblemDesc {
     int32_t w_corner;            // W(len)
     int32_t len_sum;
     int32_t has_qcorner;         // the fill records the corner's packed key (cross-check)
-    int32_t lzq;                 // line kernel: words per line in a tile's face block
+    int32_t lzq;                 // line kernels: entries per line in a tile's (column's) face block
     int32_t tb_block;            // tile-major layouts: traceback bytes per tile
     int32_t lst[MSA_MAX_K];      // tile-major layouts: byte stride of axis i inside a tile's block
     int64_t face0_stride;        // column kernel: ints per column in Q (axis-0 faces)
@@ -57,7 +58,8 @@ struct ProblemDesc {
     int32_t face1_rows;          // column kernel: skewed rows per axis-1 face
     int32_t tb_layout;           // 0: row-major (tbstride); 1: column-blocked (column kernel);
                                  // 2, 3: tile-major (generic tile kernel, line kernel)
-    int32_t pad3;
+    int32_t clear_faces;         // the encode step zeroes the column kernel's faces first (serving:
+                                 // the arena region may hold stale words of other requests)
     const uint8_t *amap;         // device 256-entry char -> code map (0xFF: invalid)
     uint8_t *codes;              // device codes
     int32_t *tab;                // device scaled pair table ((sub - 2 gap) << B)
@@ -91,7 +93,7 @@ struct LaunchDesc {
     int64_t withhold;        // test hook: this ticket never publishes (-1: off)
     int32_t nprob;
     int32_t tab_ints;        // column kernel: shared-memory ints of the replicated table
-    int32_t epoch;           // column kernel: tag of this launch's face entries (>= 1)
+    int32_t epoch;           // column and streamed line kernels: tag of this launch's face entries (>= 1)
     int32_t corner;          // column kernel: record the far corner's key (the traceback checks it)
 };
 
@@ -156,6 +158,36 @@ __host__ __device__ constexpr int line_skew_max(int K) {
     int s = 0;
     for (int i = 0; i < K - 1; ++i) s += line_ext(K, i) - 1;
     return s;
+}
+
+// Streamed line kernel (fill_lines_stream.cuh): a CTA of stream_warps(k) warps
+// sweeps a super-block of line blocks (each warp one 32-line block of the line
+// kernel, extents line_ext; the warps form a grid of extents stream_wg) over the
+// whole last axis in lockstep, in blocks of kStreamBlock steps; super-blocks
+// exchange faces as (value, epoch) entries indexed by time.
+constexpr int kStreamMinK = 4, kStreamMaxK = 5;
+constexpr int kStreamBlock = 8;  // steps per block = times per published face chunk
+__host__ __device__ constexpr int stream_wg(int K, int i) {  // warps along line axis i
+    return K == 4 ? 2 : (i < 2 ? 2 : 1);                        // k = 4: 2 x 2 x 2; k = 5: 2 x 2 x 1 x 1
+}
+__host__ __device__ constexpr int stream_warps(int K) {
+    int w = 1;
+    for (int i = 0; i < K - 1; ++i) w *= stream_wg(K, i);
+    return w;
+}
+__host__ __device__ constexpr int stream_sb(int K, int i) { return stream_wg(K, i) * line_ext(K, i); }
+__host__ __device__ constexpr int stream_skew_max(int K) {  // largest sum of local coordinates in a super-block
+    int s = 0;
+    for (int i = 0; i < K - 1; ++i) s += stream_sb(K, i) - 1;
+    return s;
+}
+__host__ __device__ constexpr int stream_face_lines(int K) {  // lines of a super-block with some c_i = SB_i - 1
+    int all = 1, inner = 1;
+    for (int i = 0; i < K - 1; ++i) {
+        all *= stream_sb(K, i);
+        inner *= stream_sb(K, i) - 1;
+    }
+    return all - inner;
 }
 
 // k = 3 column kernel geometry (shared by the planner and the kernel).
@@ -241,7 +273,7 @@ class DeviceOnce {
 // A kernel reads its per-problem IODesc from io_array[p] when io_array is set,
 // else from io_single (single-problem executions pass it by value).
 cudaError_t launch_encode(const ProblemDesc *d_probs, int nprob, int max_ncode,
-                          const IODesc *io_array, IODesc io_single, cudaStream_t s);
+                          const IODesc *io_array, IODesc io_single, cudaStream_t s, int min_blocks = 1);
 cudaError_t launch_fill_tiles(int k, int edge, const LaunchDesc &L, int grid, cudaStream_t s);
 cudaError_t prepare_kernel_attributes();
 cudaError_t traceback_attributes();
@@ -253,6 +285,8 @@ cudaError_t launch_fill_band2(const LaunchDesc &L, int grid, cudaStream_t s);
 cudaError_t launch_fill_lines(int k, int z, const LaunchDesc &L, int grid, cudaStream_t s);
 int fill_lines_ctas_per_sm(int k, int z);
 int fill_lines_warps_per_cta(int k, int z);
+cudaError_t launch_fill_stream(int k, const LaunchDesc &L, int grid, cudaStream_t s);
+int fill_stream_ctas_per_sm(int k);
 int fill_band2_ctas_per_sm();
 int fill_band2_warps_per_cta();
 int col3_smem_bytes(int alphabet_size);

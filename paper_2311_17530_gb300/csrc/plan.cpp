@@ -27,6 +27,8 @@ bool g_k3_tiles = false;
 bool g_k2_tiles = false;
 int g_line_z[MSA_MAX_K + 1] = {};            // 0: default segment
 bool g_lines_tiles[MSA_MAX_K + 1] = {};      // k = 4 .. 6: prefer the generic tile kernel
+constexpr bool kStreamDefault = true;        // the streamed form is the default at k = 4, 5
+bool g_stream[MSA_MAX_K + 1] = {false, false, false, false, kStreamDefault, kStreamDefault};
 }  // namespace
 
 int tile_edge_for(int k) {
@@ -87,11 +89,36 @@ void set_prefer_tiles_lines(int k, bool v) {
     g_lines_tiles[k] = v;
 }
 
-int choose_kernel(int k, const int32_t *lens, int A, int requested) {
+bool prefer_stream(int k) {
+    if (k < kStreamMinK || k > kStreamMaxK) return false;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    return g_stream[k];
+}
+
+void set_prefer_stream(int k, bool v) {
+    if (k < kStreamMinK || k > kStreamMaxK) return;
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_stream[k] = v;
+}
+
+void reset_prefer_stream(int k) { set_prefer_stream(k, kStreamDefault); }
+
+bool stream_fits(int k, const int32_t *lens) {
+    if (k < kStreamMinK || k > kStreamMaxK) return false;
+    // tile and super-block indices stay within 31 bits
+    int64_t tiles = 1;
+    for (int i = 0; i < k - 1; ++i) tiles *= ((int64_t)lens[i] + 1 + line_ext(k, i) - 1) / line_ext(k, i);
+    return tiles < (1LL << 31);
+}
+
+int choose_kernel(int k, const int32_t *lens, int A, int requested, bool allow_stream) {
     if (requested == kKernelTiles) return kKernelTiles;
+    if (requested == kKernelStream && k >= kStreamMinK && k <= kStreamMaxK) return kKernelStream;
     if (k >= kLinesMinK && k <= kLinesMaxK &&
-        (requested == kKernelLines || (requested == kKernelAuto && !prefer_tiles_lines(k))))
+        (requested == kKernelLines || requested == kKernelStream || (requested == kKernelAuto && !prefer_tiles_lines(k)))) {
+        if (requested == kKernelAuto && allow_stream && prefer_stream(k) && stream_fits(k, lens)) return kKernelStream;
         return kKernelLines;
+    }
     if (k == 2 && (requested == kKernelBand2 || (requested == kKernelAuto && !prefer_tiles_k2()))) return kKernelBand2;
     if (col3_fits(k, lens, A) && (requested == kKernelCol3 || !prefer_tiles_k3())) return kKernelCol3;
     return kKernelTiles;
@@ -107,6 +134,11 @@ void tile_extents(int k, const int32_t *lens, int kernel, int edge, int32_t *E) 
     if (kernel == kKernelBand2) {  // bands of 32 rows spanning every column
         E[0] = 32;
         E[1] = lens[1] + 1;
+        return;
+    }
+    if (kernel == kKernelStream) {  // 32-line blocks spanning the whole last axis
+        for (int i = 0; i < k - 1; ++i) E[i] = line_ext(k, i);
+        E[k - 1] = lens[k - 1] + 1;
         return;
     }
     if (kernel == kKernelLines) {  // 32-line blocks; the last axis cut into equal segments of at most `edge`
@@ -194,15 +226,21 @@ bool score_and_traceback_layout(HostPlan &hp) {
         hp.tb_block = (int32_t)vol;
         hp.tb_dev_bytes = hp.ntiles * vol;
     }
-    if (hp.kernel == kKernelLines) {
-        // traceback: tile t's block holds (E_{k-1} + skew_max) rows of 32 bytes,
-        // cell (c, z) at (z + sum c_i) * 32 + lane(c); faces: 32 lines of lzq words
+    if (hp.kernel == kKernelLines || hp.kernel == kKernelStream) {
+        // traceback: tile t's block holds (E_{k-1} + skew_max) rows of 32 bytes
+        // (the streamed kernel: rounded up to whole blocks), cell (c, z) at
+        // (z + sum c_i) * 32 + lane(c); faces: 32 lines of lzq words (the streamed
+        // kernel: lzq (value, tag) entries of two words)
         const int z = hp.E[k - 1];
-        hp.tb_block = (z + line_skew_max(k)) * 32;
+        const bool stream = hp.kernel == kKernelStream;
+        const int rows = z + line_skew_max(k);
+        hp.tb_block = (stream ? (rows + kStreamBlock - 1) / kStreamBlock * kStreamBlock : rows) * 32;
         hp.lst[k - 1] = 32;
         for (int i = 0; i < k - 1; ++i) hp.lst[i] = 32 + line_lstride(k, i);
-        hp.lzq = (z + 3) / 4 * 4;
-        hp.qelems = hp.ntiles * 32 * hp.lzq;
+        // streamed: lzq times per face line (the whole sweep of a super-block),
+        // stream_face_lines(k) lines per super-block
+        hp.lzq = stream ? (z + stream_skew_max(k) + kStreamBlock - 1) / kStreamBlock * kStreamBlock : (z + 3) / 4 * 4;
+        hp.qelems = stream ? hp.nunits * stream_face_lines(k) * hp.lzq * 2 : hp.ntiles * 32 * hp.lzq;
         hp.tb_layout = 3;
         hp.tb_dev_bytes = hp.ntiles * hp.tb_block;
         if (hp.qelems >= (1LL << 38) || hp.tb_dev_bytes >= (1LL << 40)) return false;
@@ -210,7 +248,8 @@ bool score_and_traceback_layout(HostPlan &hp) {
     return true;
 }
 
-int plan_shape(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err, int edge) {
+int plan_shape(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err, int edge,
+               bool allow_stream) {
     char buf[256];
     if (k < 2 || k > MSA_MAX_K) {
         snprintf(buf, sizeof buf, "k=%d outside [2,%d]", k, MSA_MAX_K);
@@ -229,7 +268,7 @@ int plan_shape(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &h
     hp = HostPlan();
     hp.k = k;
     hp.A = A;
-    hp.kernel = choose_kernel(k, lens, A, kernel_choice);
+    hp.kernel = choose_kernel(k, lens, A, kernel_choice, allow_stream);
     long double cells = 1;
     int64_t len_sum = 0, w_corner = 0, pair_min = 0;
     for (int i = 0; i < k; ++i) {
@@ -247,6 +286,11 @@ int plan_shape(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &h
     }
     if (cells > (long double)(1LL << 38) || len_sum >= (1 << 24) || w_corner >= (1 << 28)) {
         snprintf(buf, sizeof buf, "tensor of %.3Lg cells is beyond the supported size", cells);
+        err = buf;
+        return MSA_ETOOBIG;
+    }
+    if (hp.kernel == kKernelStream && !stream_fits(k, lens)) {
+        snprintf(buf, sizeof buf, "the streamed line kernel's tile indices exceed 31 bits for these lengths");
         err = buf;
         return MSA_ETOOBIG;
     }
@@ -283,8 +327,17 @@ int plan_shape(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &h
         return MSA_ETOOBIG;
     }
     hp.ntiles = nt;
+    // tickets: the tiles, or for the streamed line kernel the super-blocks of
+    // stream_wg line blocks (one CTA each)
+    int64_t nu = 1;
+    for (int i = k - 1; i >= 0; --i) {
+        hp.SG[i] = hp.kernel == kKernelStream && i < k - 1 ? (hp.G[i] + stream_wg(k, i) - 1) / stream_wg(k, i) : hp.G[i];
+        hp.sgstride[i] = nu;
+        nu *= hp.SG[i];
+    }
+    hp.nunits = nu;
     int gsum = 0;
-    for (int i = 0; i < k; ++i) gsum += hp.G[i];
+    for (int i = 0; i < k; ++i) gsum += hp.SG[i];
     hp.waves = gsum - k + 1;
 
     if (!score_and_traceback_layout(hp)) {
@@ -311,10 +364,11 @@ int plan_shape(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &h
     return MSA_OK;
 }
 
-int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err, int edge) {
-    const int rc = plan_shape(k, lens, A, kernel_choice, hp, err, edge);
+int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err, int edge,
+              bool allow_stream) {
+    const int rc = plan_shape(k, lens, A, kernel_choice, hp, err, edge, allow_stream);
     if (rc) return rc;
-    const int64_t nt = hp.ntiles;
+    const int64_t nt = hp.nunits;
     if (hp.kernel == kKernelCol3) {
         // the column order: a column (a, b) can start about a*(WR + U) + b*(32 + U)
         // CTA-time steps after the first, so tickets follow that estimate (every
@@ -348,7 +402,7 @@ int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp
             wave_of[t] = w;
             cnt[w + 1]++;
             for (int i = k - 1; i >= 0; --i) {
-                if (c[i] + 1 < hp.G[i]) {
+                if (c[i] + 1 < hp.SG[i]) {
                     ++c[i];
                     ++w;
                     break;

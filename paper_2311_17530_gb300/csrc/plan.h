@@ -10,7 +10,19 @@
 
 namespace msadp {
 
-enum FillKernel { kKernelAuto = 0, kKernelTiles = 1, kKernelCol3 = 2, kKernelBand2 = 3, kKernelLines = 4 };
+enum FillKernel {
+    kKernelAuto = 0,
+    kKernelTiles = 1,
+    kKernelCol3 = 2,
+    kKernelBand2 = 3,
+    kKernelLines = 4,
+    kKernelStream = 5,
+    kKernelCount = 6
+};
+
+// Kernels whose faces carry (value, epoch) entries: the plan clears them before
+// the first launch and gives every launch a new epoch.
+inline bool tagged_faces(int kernel) { return kernel == kKernelCol3 || kernel == kKernelStream; }
 
 struct HostPlan {
     int k = 0;
@@ -22,7 +34,10 @@ struct HostPlan {
     int32_t E[MSA_MAX_K] = {};     // tile extents
     int32_t G[MSA_MAX_K] = {};     // tile grid
     int64_t gstride[MSA_MAX_K] = {};
-    int64_t ntiles = 0;            // work units (tiles, or columns for the k=3 kernel)
+    int64_t ntiles = 0;            // tiles (columns for the k=3 kernel)
+    int64_t nunits = 0;            // tickets: ntiles, or super-blocks for the streamed line kernel
+    int32_t SG[MSA_MAX_K] = {};    // streamed line kernel: grid of super-blocks
+    int64_t sgstride[MSA_MAX_K] = {};
     int32_t waves = 0;
     int64_t qstride[MSA_MAX_K] = {};
     int64_t qelems = 0;            // score scratch elements
@@ -37,7 +52,7 @@ struct HostPlan {
     int64_t tb_dev_bytes = 0;          // device size of the traceback tensor
     int32_t tb_block = 0;              // tile-major layouts: bytes per tile
     int32_t lst[MSA_MAX_K] = {};       // tile-major layouts: byte stride of each axis inside a tile
-    int32_t lzq = 0;                   // line kernel: words per line in a tile's face block
+    int32_t lzq = 0;                   // line kernels: entries per line in a tile's (column's) face block
     int32_t edge = 0;              // tile edge of the generic kernel (tile_ext); longest segment of the
                                    // line kernel; 0 for the column and band kernels
     int32_t check_corner = 1;      // the fill records the far corner's key and the traceback checks it
@@ -68,6 +83,13 @@ int line_z_for(int k);
 int set_line_z(int k, int z);
 bool prefer_tiles_lines(int k);
 void set_prefer_tiles_lines(int k, bool v);
+// k = 4, 5: whether the automatic choice of the line kernel takes its streamed
+// form (one column per warp over the whole last axis); reset restores the default.
+bool prefer_stream(int k);
+void set_prefer_stream(int k, bool v);
+void reset_prefer_stream(int k);
+// Whether the streamed line kernel can take these lengths (32-bit face offsets).
+bool stream_fits(int k, const int32_t *lens);
 
 // Score scratch and traceback layouts from k, rho, the kernel, tile extents and
 // tile count (row-major, or tile-major for the generic kernel at k >= 4).
@@ -77,17 +99,20 @@ bool score_and_traceback_layout(HostPlan &hp);
 // Shape, limits, tile grid and layouts of one problem without the ticket order:
 // everything of make_plan that needs no heap memory. Returns MSA_OK or an MSA_E*
 // code with `err` set; edge < 0 takes the current tuned edge for k.
-int plan_shape(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err, int edge = -1);
+// allow_stream = false keeps the automatic choice off the streamed line kernel
+// (serving, whose arena regions are reused without clearing faces).
+int plan_shape(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err, int edge = -1,
+               bool allow_stream = true);
 
 // Fill `hp` for one problem: plan_shape and the ticket order. Returns MSA_OK or
 // an MSA_E* code with `err` set. edge < 0 takes the current tuned edge for k.
 int make_plan(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &hp, std::string &err,
-              int edge = -1);
+              int edge = -1, bool allow_stream = true);
 
 // Units on each wave of a grid (tiles whose coordinates sum to w), w = 0, 1, ...
 void wave_sizes(int k, const int32_t *grid, std::vector<int64_t> &out);
 
 // Which fill kernel runs for this shape when the caller leaves the choice open.
-int choose_kernel(int k, const int32_t *lens, int A, int requested);
+int choose_kernel(int k, const int32_t *lens, int A, int requested, bool allow_stream = true);
 
 }  // namespace msadp

@@ -214,7 +214,11 @@ int Server::submit(const msa_request *req, uint64_t *out) {
     }
     r->subst.assign(req->subst, req->subst + (size_t)r->A * r->A);
     std::string err;
-    rc = make_plan(r->k, r->lens.data(), r->A, (int)cfg.fill_kernel, r->hp, err);
+    // the streamed line kernel stays out of serving: its faces would have to be
+    // cleared in every reused arena region (8 bytes per cell); the line kernel
+    // synchronises by flags instead
+    const int choice = cfg.fill_kernel == kKernelStream ? kKernelLines : (int)cfg.fill_kernel;
+    rc = make_plan(r->k, r->lens.data(), r->A, choice, r->hp, err, -1, false);
     if (rc) {
         delete r;
         return set_error(rc, "%s", err.c_str());
@@ -486,6 +490,7 @@ int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg
     msa_device_result *distat = reinterpret_cast<msa_device_result *>(D + off_istat);
     msa_device_result *dres = reinterpret_cast<msa_device_result *>(D + sl.off_results);
     int64_t max_ncode = 1;
+    bool clear = false;
     for (Group &g : groups) {
         int64_t tile_base = 0;
         for (int j = 0; j < g.count; ++j) {
@@ -495,6 +500,8 @@ int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg
             size_t rb = 0;
             plan_layout(r->hp, arena_base_ + r->ws_off, &pp, &rb);
             fill_problem_desc(r->hp, pp, tile_base, hdesc[i]);
+            hdesc[i].clear_faces = r->hp.kernel == kKernelCol3 ? 1 : 0;
+            clear = clear || r->hp.kernel == kKernelCol3;
             tile_base += r->hp.ntiles;
             hdesc[i].amap = reinterpret_cast<uint8_t *>(D + off_amap + (size_t)i * 256);
             hdesc[i].istat = distat + i;
@@ -550,7 +557,7 @@ int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg
     int rc = MSA_OK;
     if (e == cudaSuccess) e = cudaMemcpyAsync(D, H, in_bytes, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(D + off_state, 0, zero_bytes, s);
-    if (e == cudaSuccess) e = launch_encode(ddesc, n, max_ncode, dio, IODesc{}, s);
+    if (e == cudaSuccess) e = launch_encode(ddesc, n, max_ncode, dio, IODesc{}, s, clear ? 32 : 1);
     for (size_t gi = 0; gi < groups.size() && e == cudaSuccess; ++gi) {
         const Group &g = groups[gi];
         LaunchDesc L;

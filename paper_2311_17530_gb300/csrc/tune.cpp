@@ -1,7 +1,8 @@
 // Autotuner of the tile shape: the paper fixes its partition size S by hand
 // (section 3.2's example uses S = 3); here each k has a few compiled tile edges
 // (tile_edge_candidate) and, for k = 3, the column kernel (k = 2: the band
-// kernel; k = 4 .. 6: the line kernel's compiled segment lengths). msa_autotune times
+// kernel; k = 4 .. 6: the line kernel's compiled segment lengths, and at k = 4, 5
+// its streamed form). msa_autotune times
 // every candidate on a synthetic problem of the caller's shape -- plan creation,
 // then repeated executions of encode, fill and traceback between CUDA events --
 // and makes the fastest the choice for k in every later plan and serving batch.
@@ -81,7 +82,10 @@ int msa_get_tile_edge(int k, int32_t *out_edge) {
 
 int msa_set_line_segment(int k, int32_t z) {
     if (set_line_z(k, z) != MSA_OK) return set_error(MSA_EINVAL, "line segment %d is not compiled for k=%d", z, k);
-    if (z == 0) set_prefer_tiles_lines(k, false);  // defaults: the line kernel for k = 4 .. 6
+    if (z == 0) {  // defaults: the line kernel for k = 4 .. 6, streamed at k = 4, 5
+        set_prefer_tiles_lines(k, false);
+        reset_prefer_stream(k);
+    }
     return MSA_OK;
 }
 
@@ -141,6 +145,7 @@ int msa_autotune(int k, const int32_t *lens, int alphabet_size, int32_t repeats,
     if (k == 2) cands.push_back({kKernelBand2, 0});
     for (int i = 0; i < kMaxLineSegments; ++i)
         if (line_z_candidate(k, i) > 0) cands.push_back({kKernelLines, line_z_candidate(k, i)});
+    if (k >= kStreamMinK && k <= kStreamMaxK && stream_fits(k, lens)) cands.push_back({kKernelStream, 0});
     int best = -1;
     for (const Cand &c : cands) {
         if (out->ncand >= MSA_MAX_TUNING_CANDIDATES) break;
@@ -163,12 +168,23 @@ int msa_autotune(int k, const int32_t *lens, int alphabet_size, int32_t repeats,
         if (k == 3) set_prefer_tiles_k3(true);
         if (k == 2) set_prefer_tiles_k2(true);
         set_prefer_tiles_lines(k, true);
+        set_prefer_stream(k, false);
     } else {
         if (k == 3) set_prefer_tiles_k3(false);
         if (k == 2) set_prefer_tiles_k2(false);
         if (out->cand_kernel[best] == kKernelLines) {
             set_line_z(k, out->cand_edge[best]);
             set_prefer_tiles_lines(k, false);
+            set_prefer_stream(k, false);
+        }
+        if (out->cand_kernel[best] == kKernelStream) {
+            set_prefer_tiles_lines(k, false);
+            set_prefer_stream(k, true);
+            // the best segmented candidate stays the choice where the streamed one cannot run (serving)
+            int bl = -1;
+            for (int i = 0; i < out->ncand; ++i)
+                if (out->cand_kernel[i] == kKernelLines && (bl < 0 || out->cand_ms[i] < out->cand_ms[bl])) bl = i;
+            if (bl >= 0) set_line_z(k, out->cand_edge[bl]);
         }
         // the best generic edge stays the fallback for shapes the column kernel cannot take
         int bt = -1;

@@ -309,7 +309,7 @@ def msa_autotune(lens: Sequence[int], alphabet_size: int, repeats: int = 3) -> d
     shape; the fastest becomes the choice for k. Returns the candidates and the choice."""
     t = Tuning()
     _check(library().msa_autotune(len(lens), _i32(lens), int(alphabet_size), int(repeats), ctypes.byref(t)))
-    names = {1: "tiles", 2: "column", 3: "band", 4: "lines"}
+    names = {1: "tiles", 2: "column", 3: "band", 4: "lines", 5: "stream"}
     cands = [{"kernel": names[int(t.cand_kernel[i])], "edge": int(t.cand_edge[i]),
               "ms": float(t.cand_ms[i])} for i in range(t.ncand)]
     return {"k": int(t.k), "lens": list(lens), "candidates": cands, "best": cands[t.best]}

@@ -1,7 +1,7 @@
 """The library's limits, bit-exact against the oracle: the column kernel's
 largest last axis (4096 positions) and largest alphabet (24 letters; 25 falls
 back to the generic kernel), the largest alphabet the ABI takes (32 letters,
-through the generic tile kernel and the line kernel),
+through the generic tile kernel and both line kernels),
 and a long two-sequence problem over several tile waves."""
 import numpy as np
 import pytest
@@ -53,9 +53,10 @@ def test_column_kernel_largest_alphabet(size, kernel):
     run_full(alphabet_problem(5100 + size, 3, [45, 37, 52], size), want_kernel=kernel)
 
 
-@pytest.mark.parametrize("kernel", [1, 4])
+@pytest.mark.parametrize("kernel", [1, 4, 5])
 def test_largest_alphabet_generic_and_line_kernels(kernel):
-    """32 letters at k = 4 through the generic tile kernel (1) and the line kernel (4)."""
+    """32 letters at k = 4 through the generic tile kernel (1), the line kernel (4)
+    and the streamed line kernel (5)."""
     msa.msa_config("fill_kernel", kernel)
     try:
         run_full(alphabet_problem(5200, 4, [13, 11, 14, 40], 32), want_kernel=kernel)

@@ -111,17 +111,25 @@ def test_plan_reuse_is_deterministic():
     np.testing.assert_array_equal(a[3], b[3])
 
 
-@pytest.mark.parametrize("name", ["pr1", "k2_protein", "k3_protein", "k4_dna", "k6_protein"])
-def test_full_size_workloads_against_stored_oracle_values(name):
+@pytest.mark.parametrize("name,kernel", [("pr1", 0), ("k2_protein", 0), ("k3_protein", 0), ("k4_dna", 4),
+                                         ("k4_dna", 5), ("k6_protein", 0)])
+def test_full_size_workloads_against_stored_oracle_values(name, kernel):
     """Full-size workloads: score, alignment and sampled traceback bytes against
-    values written by tests/golden/make_golden.py (oracle only)."""
+    values written by tests/golden/make_golden.py (oracle only); k = 4 DNA through
+    both line kernels (segmented and streamed)."""
     path = os.path.join(GOLDEN, f"{name}.json")
     if not os.path.exists(path):
         pytest.skip(f"{path} not generated")
     g = json.load(open(path))
     p = inputs.WORKLOADS[name]()
     assert p.lens == g["lens"]
-    score, rows, status, tb = run_plan(p, want_tb=True)
+    msa.msa_config("fill_kernel", kernel)
+    try:
+        with msa.Plan(p.k, p.lens, p.alphabet) as plan:
+            assert kernel == 0 or plan.info().fill_kernel == kernel
+            score, rows, status, tb = run_plan(p, plan=plan, want_tb=True)
+    finally:
+        msa.msa_config("fill_kernel", 0)
     assert status == 0
     assert score == g["score"]
     assert rows == oracle.expand(p.seqs, bytes.fromhex(g["masks_hex"]))
@@ -228,7 +236,8 @@ def test_k3_auto_picks_column_kernel():
 
 
 @pytest.mark.parametrize("kernel,k,lens", [(2, 3, [40, 37, 45]), (2, 3, [63, 95, 70]), (3, 2, [150, 170]),
-                                           (3, 2, [33, 400]), (4, 4, [9, 13, 10, 40]), (1, 4, [9, 13, 10, 40])])
+                                           (3, 2, [33, 400]), (4, 4, [9, 13, 10, 40]), (1, 4, [9, 13, 10, 40]),
+                                           (5, 4, [9, 13, 10, 40]), (5, 5, [5, 4, 5, 9, 40])])
 def test_every_fill_kernel_records_the_corner_key(kernel, k, lens):
     """Every fill kernel records the far corner's packed key; the traceback
     compares the rescored path with it. A consistent result (status 0, the
@@ -249,7 +258,8 @@ def test_every_fill_kernel_records_the_corner_key(kernel, k, lens):
 
 @pytest.mark.parametrize("seed", [3, 99])
 @pytest.mark.parametrize("kernel,k,lens", [(2, 3, [70, 65, 90]), (3, 2, [150, 170]), (1, 3, [30, 25, 28]),
-                                           (1, 4, [9, 8, 10, 7]), (1, 5, [5, 4, 6, 5, 4])])
+                                           (1, 4, [9, 8, 10, 7]), (1, 5, [5, 4, 6, 5, 4]),
+                                           (5, 4, [9, 13, 10, 70]), (5, 5, [5, 4, 5, 9, 40])])
 def test_shuffled_orders_over_a_poisoned_traceback(kernel, k, lens, seed):
     """Tickets permuted inside every wave (another topological order of the same
     tiles or columns) and the traceback tensor filled with 0xFF before the fill:

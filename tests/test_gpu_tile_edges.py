@@ -72,14 +72,18 @@ def test_autotune_picks_the_fastest_and_plans_follow():
         plan.close()
     res4 = msa.msa_autotune([30, 32, 34, 36], 4, repeats=2)
     assert {(c["kernel"], c["edge"]) for c in res4["candidates"]} == {("tiles", 4), ("tiles", 5), ("tiles", 6),
-                                                                      ("lines", 8), ("lines", 16), ("lines", 32)}
+                                                                      ("lines", 8), ("lines", 16), ("lines", 32),
+                                                                      ("stream", 0)}
     best4 = res4["best"]
     if best4["kernel"] == "tiles":
         assert msa.msa_get_tile_edge(4) == best4["edge"]
-    else:
+    elif best4["kernel"] == "lines":
         assert msa.msa_get_line_segment(4) == best4["edge"]
+    else:  # the streamed kernel: the best segment stays the choice where it cannot run
+        lines = [c for c in res4["candidates"] if c["kernel"] == "lines"]
+        assert msa.msa_get_line_segment(4) == min(lines, key=lambda c: c["ms"])["edge"]
     with msa.Plan(4, [30, 32, 34, 36], inputs.DNA) as plan4:
-        assert plan4.info().fill_kernel == (1 if best4["kernel"] == "tiles" else 4)
+        assert plan4.info().fill_kernel == {"tiles": 1, "lines": 4, "stream": 5}[best4["kernel"]]
     # the tuned shape still gives the oracle's answer
     p = inputs.random_problem(3100, 4, [14, 17, 15, 13], related=True)
     want = oracle.align(p.seqs, p.alphabet, p.subst, p.gap)
