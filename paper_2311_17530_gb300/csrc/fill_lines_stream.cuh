@@ -97,12 +97,18 @@ struct StreamLayout {
     static constexpr int NH = stream_halo_lines<K>();
     static constexpr int NFL = stream_face_lines(K);
     static constexpr int NROW = stream_rows<K>();
-    // pair-table row stride: at least 32, rows staggered by (a line block's skew) + 1 banks
-    static constexpr int ZS = 32 + line_skew_max(K) + 1;
+    // pair-table rows: a 32-position ring stored twice (slots p mod 32 and
+    // p mod 32 + 32, so that a block's positions need no wrap), rows staggered by
+    // (a line block's skew) + 1 banks
+    static constexpr int ZS = 64 + line_skew_max(K) + 1;
+    static constexpr int NT = 32 * stream_warps(K);
+    static constexpr int HC = (NH * (kStreamU / 2) + NT - 1) / NT;  // halo copies per thread and block
     static constexpr int V = 0;
     static constexpr int PT = V + stream_ring_words<K>();
     static constexpr int STAGE = PT + round_up(NROW * ZS, 4);
-    static constexpr int HTAB = STAGE + NH * kStreamU * 2;
+    static constexpr int HOFS = STAGE + NH * kStreamU * 2;  // per thread and copy: source offset (8 bytes)
+    static constexpr int HMETA = HOFS + 2 * HC * NT;        // ... ring base | time offset << 13
+    static constexpr int HTAB = HMETA + HC * NT;
     static constexpr int FTAB = HTAB + round_up(NH, 4);
     static constexpr int NB = FTAB + round_up(NFL, 4);
     static constexpr int CROW = NB + round_up(1 << (K - 1), 4);
@@ -155,7 +161,7 @@ __global__ void __launch_bounds__(stream_threads<K>(), stream_min_ctas<K>()) fil
     using LY = StreamLayout<K>;
     constexpr int NH = LY::NH, NFL = LY::NFL, NROW = LY::NROW, ZS = LY::ZS;
     constexpr int NP = NH * (U / 2);         // halo copies (two entries each) per block
-    constexpr int HC = (NP + NT - 1) / NT;   // ... per thread
+    constexpr int HC = LY::HC;               // ... per thread
     constexpr int NF = NFL * (U / 2);        // face stores (two entries each) per block
     constexpr int FC = (NF + NT - 1) / NT;   // ... per thread
     constexpr int PQ = (NROW * U + NT - 1) / NT;  // pair-table entries per thread and refill
@@ -163,13 +169,16 @@ __global__ void __launch_bounds__(stream_threads<K>(), stream_min_ctas<K>()) fil
     // times (2U slots suffice); the pair-table ring holds the positions a block
     // reads, bU - SMAX .. bU + U - 1, and after the block the next U positions
     // replace positions below (b + 1) U - SMAX (32 slots suffice).
-    static_assert(2 * U <= D && SMAX + U <= 32 && NFL < 128 && LY::PT < (1 << 13), "geometry");
+    static_assert(2 * U <= D && SMAX + U <= 32 && NFL < 128 && LY::PT < (1 << 13) && NT % (U / 2) == 0,
+                  "geometry");
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int32_t *sm = reinterpret_cast<int32_t *>(smem_raw);
     int32_t *V = sm + LY::V;
     int32_t *PT = sm + LY::PT;
     unsigned long long *stage = reinterpret_cast<unsigned long long *>(sm + LY::STAGE);
+    int64_t *hofs = reinterpret_cast<int64_t *>(sm + LY::HOFS);
+    int32_t *hmeta = sm + LY::HMETA;
     // halo lines: ring base | producer face line << 13 | axes at -1 << 20
     uint32_t *htab = reinterpret_cast<uint32_t *>(sm + LY::HTAB);
     uint32_t *ftab = reinterpret_cast<uint32_t *>(sm + LY::FTAB);  // face lines: ring base
@@ -353,22 +362,30 @@ __global__ void __launch_bounds__(stream_threads<K>(), stream_min_ctas<K>()) fil
                 if ((S >> i) & 1) s += stream_sb(K, i);
             return s;
         };
-        auto halo_src = [&](int idx, int c) -> const unsigned long long * {
-            const uint32_t e = htab[idx / (U / 2)];
-            const uint32_t S = (e >> 20) & 15;
-            const int src = nb[S];
-            const int tp = c * U + 2 * (idx % (U / 2)) + sb_of(S);
-            if (src < 0 || tp < 0 || tp >= ZQ) return nullptr;
-            return Fq + (int64_t)src * FB + (int64_t)((e >> 13) & 127) * ZQ + tp;
-        };
+        // this thread's copies, once per column: the source face line's offset
+        // (-1: no producer) and the ring base | the time offset SB_S + 2 q2
+        const int q2 = tid % (U / 2);  // the same for every copy of this thread
+#pragma unroll
+        for (int v = 0; v < HC; ++v) {
+            const int idx = tid + NT * v;
+            if (idx < NP) {
+                const uint32_t e = htab[idx / (U / 2)];
+                const uint32_t S = (e >> 20) & 15;
+                const int src = nb[S];
+                hofs[v * NT + tid] = src < 0 ? -1 : (int64_t)src * FB + (int64_t)((e >> 13) & 127) * ZQ;
+                hmeta[v * NT + tid] = (int)(e & 0x1FFF) | (2 * q2 + sb_of(S)) << 13;
+            }
+        }
+        // copy pair v of consumer chunk c when its producer time lies in the sweep
         auto halo_issue = [&](int c, bool mine) {
             if (mine) {
 #pragma unroll
                 for (int v = 0; v < HC; ++v) {
                     const int idx = tid + NT * v;
                     if (idx < NP) {
-                        const unsigned long long *g = halo_src(idx, c);
-                        if (g) cp_async16(stage + 2 * idx, g);
+                        const int64_t o = hofs[v * NT + tid];
+                        const int tp = c * U + (hmeta[v * NT + tid] >> 13);
+                        if (o >= 0 && (unsigned)tp < (unsigned)ZQ) cp_async16(stage + 2 * idx, Fq + o + tp);
                     }
                 }
             }
@@ -409,10 +426,11 @@ __global__ void __launch_bounds__(stream_threads<K>(), stream_min_ctas<K>()) fil
                 for (int v = 0; v < HC; ++v) {
                     const int idx = tid + NT * v;
                     if (idx < NP) {
-                        const int tc = c * U + 2 * (idx % (U / 2));
-                        const int base = (int)(htab[idx / (U / 2)] & 0x1FFF);
+                        const int tc = c * U + 2 * q2;
+                        const int meta = hmeta[v * NT + tid];
+                        const int base = meta & 0x1FFF, tp = c * U + (meta >> 13);
                         int v0 = kNeg, v1 = kNeg;
-                        if (halo_src(idx, c)) {
+                        if (hofs[v * NT + tid] >= 0 && (unsigned)tp < (unsigned)ZQ) {
                             const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(stage + 2 * idx);
                             ok = ok && (int)(x.x >> 32) == epoch && (int)(x.y >> 32) == epoch;
                             v0 = (int)(unsigned)x.x;
@@ -467,7 +485,10 @@ __global__ void __launch_bounds__(stream_threads<K>(), stream_min_ctas<K>()) fil
 #pragma unroll
             for (int u = 0; u < PQ; ++u) {
                 const int it = tid + NT * u, p = p0 + it % U;
-                if (it < NROW * U && p < rho) PT[(it / U) * ZS + (p & 31)] = pent[u];
+                if (it < NROW * U && p < rho) {
+                    PT[(it / U) * ZS + (p & 31)] = pent[u];
+                    PT[(it / U) * ZS + (p & 31) + 32] = pent[u];
+                }
             }
         };
 
@@ -513,49 +534,57 @@ __global__ void __launch_bounds__(stream_threads<K>(), stream_min_ctas<K>()) fil
             bool issued = false;
             const int Wb0 = Wl + b * U * (1 << NA);
             const int r0 = b * U - sigw;  // traceback row of step bU
+            const int zp0 = (b * U - sig) & 31;
+            const int32_t *ptb[NA];
+#pragma unroll
+            for (int i = 0; i < NA; ++i) ptb[i] = ptrow[i] + zp0;
 #pragma unroll
             for (int s = 0; s < U; ++s) {
-                if (s == 3) {
-                    if (want && warp == 0) {
-                        const bool r = __all_sync(kFull, my_src < 0 || count_ok(cnt, b + 1));
-                        if (lane == 0) misc[1] = r;
-                    }
-                    if (refill) pt_entries();
+                // checkpoints: warp 0 judges the counts at steps 2 and 5, every
+                // thread reads the verdict after that step's barrier
+                if ((s == 2 || s == 5) && want && !issued && warp == 0) {
+                    const bool r = __all_sync(kFull, my_src < 0 || count_ok(cnt, b + 1));
+                    if (lane == 0) misc[1] = r;
+                    if (!r && my_src >= 0) cnt = ld_relaxed(prog + my_src);
                 }
-                if (s == 4 && want) {  // the verdict of step 3 is visible after its barrier
+                if ((s == 3 || s == 6) && want && !issued) {
                     issued = misc[1] != 0;
                     if (issued) halo_issue(b + 1, true);
                 }
+                if (s == 3 && refill) pt_entries();
                 const int ts = b * U + s;
-                const int z = ts - sig;
-                const bool act = (unsigned)z < (unsigned)rho;
-                const int zp = z & 31;
-                int p[NA];
+                // a warp none of whose lanes holds a cell at this step skips it (every
+                // thread still meets the step's one barrier)
+                if ((unsigned)(ts - sigw) < (unsigned)(rho + line_skew_max(K))) {
+                    const int z = ts - sig;
+                    const bool act = (unsigned)z < (unsigned)rho;
+                    int p[NA];
 #pragma unroll
-                for (int i = 0; i < NA; ++i) p[i] = ptrow[i][zp];
-                int T[M + 1];
-                T[0] = 0;
+                    for (int i = 0; i < NA; ++i) p[i] = ptb[i][s];
+                    int T[M + 1];
+                    T[0] = 0;
 #pragma unroll
-                for (int m = 1; m <= M; ++m) T[m] = (m & (m - 1)) ? T[m & (m - 1)] + p[lowbit_c(m)] : p[lowbit_c(m)];
-                int acc0 = vself, acc1 = kNeg;
+                    for (int m = 1; m <= M; ++m) T[m] = (m & (m - 1)) ? T[m & (m - 1)] + p[lowbit_c(m)] : p[lowbit_c(m)];
+                    int acc0 = vself, acc1 = kNeg;
 #pragma unroll
-                for (int m = 1; m <= M; ++m) {
-                    const int slot = (PAR * U + s - popc_c(m)) & (D - 1);
-                    const int cm = vb[slot - stream_move_off<K>(m)] + Sp[m];
-                    const int cb = carry[m] + T[m];
-                    if (m & 1)
-                        acc0 = __vimax3_s32(acc0, cm, cb);
-                    else
-                        acc1 = __vimax3_s32(acc1, cm, cb);
-                    carry[m] = cm;
-                }
-                const int acc = max(acc0, acc1);
-                const int tm = (Wb0 + s * (1 << NA) - acc) & MASKB;
-                const int val = acc + tm;
-                if (has_tile && (unsigned)(r0 + s) < (unsigned)rows) tbw[(int64_t)(r0 + s) * 32] = (uint8_t)tm;
-                if (act) {
-                    vb[(PAR * U + s) & (D - 1)] = val;
-                    vself = val;
+                    for (int m = 1; m <= M; ++m) {
+                        const int slot = (PAR * U + s - popc_c(m)) & (D - 1);
+                        const int cm = vb[slot - stream_move_off<K>(m)] + Sp[m];
+                        const int cb = carry[m] + T[m];
+                        if (m & 1)
+                            acc0 = __vimax3_s32(acc0, cm, cb);
+                        else
+                            acc1 = __vimax3_s32(acc1, cm, cb);
+                        carry[m] = cm;
+                    }
+                    const int acc = max(acc0, acc1);
+                    const int tm = (Wb0 + s * (1 << NA) - acc) & MASKB;
+                    const int val = acc + tm;
+                    if (has_tile && (unsigned)(r0 + s) < (unsigned)rows) tbw[(int64_t)(r0 + s) * 32] = (uint8_t)tm;
+                    if (act) {
+                        vb[(PAR * U + s) & (D - 1)] = val;
+                        vself = val;
+                    }
                 }
                 __syncthreads();
             }
