@@ -77,6 +77,35 @@ extern "C" {
 int msa_align(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
               const int32_t *subst, int32_t gap, int32_t *out_score, char *out_alignment);
 
+/*
+ * Every alignment scoring at least OPT - delta (delta >= 0; delta = 0: every
+ * optimal alignment), the further optimal and near-optimal solutions the paper
+ * proposes to retrieve by forking at equally ranked paths or within a user
+ * threshold (section 6). The fill keeps every cell's score (the generic tile
+ * kernel); a walk on the device from the far corner follows a move only when the
+ * best completion through its predecessor still reaches OPT - delta, trying the
+ * moves of each column in increasing mask order, so alignments come in
+ * increasing lexicographic order of their reversed column sequence (for
+ * delta = 0 the first is msa_align's).
+ *
+ *   k, seqs, lens, alphabet, subst, gap   as for msa_align
+ *   delta       score threshold below the optimum
+ *   max_count   alignments to store, >= 1
+ *   out_masks   max_count x sum(lens) bytes: alignment a's move masks, first column
+ *               first, at a * sum(lens) (bit i set: sequence i consumes a residue)
+ *   out_ncols   max_count: alignment a's column count
+ *   out_scores  max_count: alignment a's SP score
+ *   out_count   alignments stored
+ *   out_more    1 when the walk stopped at max_count with more alignments left
+ *
+ * Host buffers; allocates device memory for the call and frees it; synchronous.
+ * Errors as msa_align; MSA_EINVAL also for delta < 0, max_count < 1 or NULL
+ * outputs.
+ */
+int msa_near_optimal(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
+                     const int32_t *subst, int32_t gap, int64_t delta, int32_t max_count, uint8_t *out_masks,
+                     int32_t *out_ncols, int64_t *out_scores, int32_t *out_count, int32_t *out_more);
+
 /* Thread-local description of the last failure in this thread ("" if none). */
 const char *msa_last_error(void);
 

@@ -643,6 +643,97 @@ int msa_align(int k, const char *const *seqs, const int32_t *lens, const char *a
 }
 
 // ---------------------------------------------------------------------------
+// msa_near_optimal: every alignment within delta of the optimum (host buffers).
+
+int msa_near_optimal(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
+                     const int32_t *subst, int32_t gap, int64_t delta, int32_t max_count, uint8_t *out_masks,
+                     int32_t *out_ncols, int64_t *out_scores, int32_t *out_count, int32_t *out_more) {
+    uint8_t amap[256];
+    int rc = validate_request(k, seqs, lens, alphabet, subst, amap);
+    if (rc) return rc;
+    if (delta < 0 || max_count < 1 || !out_masks || !out_ncols || !out_scores || !out_count || !out_more)
+        return set_error(MSA_EINVAL, "delta < 0, max_count < 1 or a NULL output pointer");
+    // the generic tile kernel keeps every cell's score, which the walk reads
+    msa_plan *plan = nullptr;
+    rc = plan_create(k, lens, alphabet, kKernelTiles, -1, &plan);
+    if (rc) return rc;
+    const int A = plan->hp.A;
+    const size_t total = (size_t)plan->hp.len_sum;
+    if ((double)max_count * (double)(total + 1) > (double)(1LL << 36)) {
+        msa_plan_destroy(plan);
+        return set_error(MSA_ETOOBIG, "max_count x (sum of lengths) is beyond the supported output size");
+    }
+    // one device buffer: inputs, the single-alignment outputs, the enumeration's
+    // outputs and its stack
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    const size_t o_res = take(total + 16), o_sub = take((size_t)A * A * 4), o_out = take(sizeof(msa_device_result)),
+                 o_mask1 = take(total + 16), o_masks = take((size_t)max_count * total + 16),
+                 o_ncols = take((size_t)max_count * 4), o_scores = take((size_t)max_count * 8), o_cm = take(8),
+                 o_path = take(total + 16), o_acc = take((total + 1) * 8), o_next = take((total + 1) * 4);
+    char *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        msa_plan_destroy(plan);
+        return set_error(MSA_ENOMEM, "near-optimal buffers: %s", cudaGetErrorString(e));
+    }
+    std::vector<char> res(total + 1);
+    size_t o = 0;
+    for (int i = 0; i < k; ++i) {
+        if (lens[i]) memcpy(res.data() + o, seqs[i], (size_t)lens[i]);
+        o += (size_t)lens[i];
+    }
+    cudaStream_t s = library_stream(&rc);
+    if (!rc) {
+        e = cudaMemcpy(d + o_res, res.data(), total, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d + o_sub, subst, (size_t)A * A * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = cuda_error(e, "near-optimal inputs");
+    }
+    if (!rc)
+        rc = msa_plan_execute(plan, d + o_res, reinterpret_cast<const int32_t *>(d + o_sub), gap,
+                              reinterpret_cast<msa_device_result *>(d + o_out), reinterpret_cast<uint8_t *>(d + o_mask1),
+                              s);
+    if (!rc) {
+        IODesc io{d + o_res, reinterpret_cast<const int32_t *>(d + o_sub),
+                  reinterpret_cast<msa_device_result *>(d + o_out), reinterpret_cast<uint8_t *>(d + o_mask1), gap, 0};
+        NearOut no{reinterpret_cast<uint8_t *>(d + o_masks), reinterpret_cast<int32_t *>(d + o_ncols),
+                   reinterpret_cast<int64_t *>(d + o_scores), reinterpret_cast<int32_t *>(d + o_cm),
+                   reinterpret_cast<uint8_t *>(d + o_path), reinterpret_cast<int64_t *>(d + o_acc),
+                   reinterpret_cast<int32_t *>(d + o_next)};
+        e = launch_near_optimal(plan->pp.prob, io, delta, max_count, no, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = cuda_error(e, "near-optimal enumeration");
+    }
+    msa_device_result r;
+    int32_t cm[2] = {0, 0};
+    if (!rc) {
+        e = cudaMemcpy(&r, d + o_out, sizeof r, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(cm, d + o_cm, 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_error(e, "near-optimal results");
+    }
+    if (!rc) rc = status_error(r.status);
+    if (!rc && cm[1] == 2) rc = set_error(MSA_ECUDA, "near-optimal walk found an inconsistent score tensor");
+    if (!rc && cm[0] > 0) {
+        e = cudaMemcpy(out_masks, d + o_masks, (size_t)cm[0] * total, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(out_ncols, d + o_ncols, (size_t)cm[0] * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(out_scores, d + o_scores, (size_t)cm[0] * 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = cuda_error(e, "near-optimal results");
+    }
+    if (!rc) {
+        *out_count = cm[0];
+        *out_more = cm[1];
+    }
+    cudaFree(d);
+    msa_plan_destroy(plan);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
 // Host-only planner queries.
 
 int msa_wave_sizes(int k, const int32_t *grid, int64_t *out_sizes, int32_t max_waves, int32_t *out_waves) {

@@ -290,6 +290,21 @@ int fill_stream_ctas_per_sm(int k);
 int fill_band2_ctas_per_sm();
 int fill_band2_warps_per_cta();
 int col3_smem_bytes(int alphabet_size);
+// Outputs and stack of the near-optimal enumeration (near_optimal.cu), device memory:
+// masks max_count x len_sum (first column first), ncols and scores per alignment,
+// count_more[2] = {alignments stored, 1 when more were left (2: walk inconsistent)},
+// and per depth (len_sum + 1 entries) the move taken, the score so far and the next mask.
+struct NearOut {
+    uint8_t *masks;
+    int32_t *ncols;
+    int64_t *scores;
+    int32_t *count_more;
+    uint8_t *path;
+    int64_t *acc;
+    int32_t *next;
+};
+cudaError_t launch_near_optimal(const ProblemDesc *d_prob, IODesc io, int64_t delta, int32_t max_count, NearOut o,
+                                cudaStream_t s);
 cudaError_t launch_traceback(const ProblemDesc *d_probs, int nprob, const int32_t *err,
                              const IODesc *io_array, IODesc io_single, cudaStream_t s);
 

@@ -33,7 +33,7 @@ EXPORTED = ["msa_align", "msa_last_error", "msa_set_stream", "msa_config", "msa_
             "msa_cancel", "msa_drain", "msa_wave_sizes", "msa_tile_shape", "msa_version",
             "msa_plan_read_tb", "msa_plan_timings", "msa_align_noalloc", "msa_wait_any",
             "msa_set_tile_edge", "msa_get_tile_edge", "msa_set_line_segment", "msa_get_line_segment",
-            "msa_autotune"]
+            "msa_autotune", "msa_near_optimal"]
 
 
 class MsaError(RuntimeError):
@@ -82,6 +82,9 @@ def library() -> ctypes.CDLL:
     i32p = ctypes.POINTER(ctypes.c_int32)
     L.msa_align.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), i32p, ctypes.c_char_p, i32p,
                             ctypes.c_int32, i32p, ctypes.c_char_p]
+    L.msa_near_optimal.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), i32p, ctypes.c_char_p, i32p,
+                                   ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, i32p, i32p]
     L.msa_last_error.restype = ctypes.c_char_p
     L.msa_version.restype = ctypes.c_char_p
     L.msa_set_stream.argtypes = [ctypes.c_void_p]
@@ -154,6 +157,38 @@ def msa_align(seqs: Sequence[str], alphabet: str, subst, gap: int) -> Tuple[int,
     score = ctypes.c_int32(0)
     _check(L.msa_align(k, arr, lens, alphabet.encode(), _table(subst), int(gap), ctypes.byref(score), out))
     return int(score.value), _rows(out.raw, k, stride)
+
+
+def msa_near_optimal(seqs: Sequence[str], alphabet: str, subst, gap: int, delta: int = 0,
+                     max_count: int = 64) -> Tuple[List[Tuple[int, List[int], List[str]]], bool]:
+    """Every alignment within ``delta`` of the optimum through the C-ABI call:
+    ([(score, masks first column first, rows)], more)."""
+    L = library()
+    k = len(seqs)
+    enc = [s.encode() for s in seqs]
+    arr = (ctypes.c_char_p * max(1, k))(*enc)
+    lens = _i32([len(s) for s in enc])
+    total = sum(len(s) for s in enc)
+    masks = np.zeros((max_count, max(1, total)), dtype=np.uint8)
+    ncols = np.zeros(max_count, dtype=np.int32)
+    scores = np.zeros(max_count, dtype=np.int64)
+    count, more = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(L.msa_near_optimal(k, arr, lens, alphabet.encode(), _table(subst), int(gap), int(delta), int(max_count),
+                              masks.ctypes.data, ncols.ctypes.data, scores.ctypes.data, ctypes.byref(count),
+                              ctypes.byref(more)))
+    out = []
+    for a in range(count.value):
+        ms = [int(m) for m in masks[a, : ncols[a]]]
+        rows, pos = [[] for _ in range(k)], [0] * k
+        for m in ms:
+            for i in range(k):
+                if (m >> i) & 1:
+                    rows[i].append(seqs[i][pos[i]])
+                    pos[i] += 1
+                else:
+                    rows[i].append("-")
+        out.append((int(scores[a]), ms, ["".join(r) for r in rows]))
+    return out, bool(more.value)
 
 
 def msa_config(key: str, value: int) -> None:
