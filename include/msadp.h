@@ -106,6 +106,50 @@ int msa_near_optimal(int k, const char *const *seqs, const int32_t *lens, const 
                      const int32_t *subst, int32_t gap, int64_t delta, int32_t max_count, uint8_t *out_masks,
                      int32_t *out_ncols, int64_t *out_scores, int32_t *out_count, int32_t *out_more);
 
+/*
+ * Exact search-space pruning (section 6 proposes searching only the partitions
+ * where an optimal alignment can lie). Any alignment through cell x scores at
+ * most U(x) = sum over pairs i < j of fwd_ij(x_i, x_j) + bwd_ij(x_i, x_j), the
+ * optimal pairwise scores of the prefixes and suffixes (Eq. 1 on each pair; gap
+ * against gap scores 0, section 5.2). The fill is the generic tile kernel; a
+ * tile whose bound -- the sum over pairs of the largest fwd + bwd over the tile's
+ * rectangle -- is below a lower bound L on the optimum holds no cell of an
+ * optimal alignment and is left out. The score and alignment equal msa_align's
+ * (the same tie rule) whenever L does not exceed the optimum.
+ *
+ *   have_lower_bound  0: L is the score of a feasible alignment the device builds
+ *                     from the origin, taking at each cell the move to the
+ *                     neighbour with the largest U (ties: lowest mask);
+ *                     1: L = lower_bound (e.g. the score of a heuristic alignment)
+ *   out_score, out_alignment  as for msa_align
+ *   out_stats         (may be NULL) the bound used and what was left out
+ *
+ * Sequences of at most 16383 residues. Host buffers; allocates device memory for
+ * the call; synchronous. MSA_EINVAL also when a given lower bound exceeds the
+ * optimum (detected after the fill).
+ */
+typedef struct msa_prune_stats {
+    int64_t lower_bound;   /* L */
+    int64_t tiles;         /* tiles of the fill */
+    int64_t tiles_skipped; /* tiles left out */
+    int64_t cells_skipped; /* cells of the tensor in them */
+    int64_t cells;         /* cells of the tensor */
+} msa_prune_stats;
+int msa_align_pruned(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
+                     const int32_t *subst, int32_t gap, int32_t have_lower_bound, int64_t lower_bound,
+                     int32_t *out_score, char *out_alignment, msa_prune_stats *out_stats);
+
+/*
+ * The pruning bound of every tile of extents `extents` (k entries >= 1; tile grid
+ * G_i = ceil((len_i + 1) / extents_i), tiles numbered row-major, last axis
+ * fastest), computed on the device as msa_align_pruned does:
+ * out_bounds[t] = sum over pairs i < j of the largest fwd_ij + bwd_ij over the
+ * tile's range of axis i times its range of axis j. out_bounds holds prod G_i
+ * entries. Sequences of at most 16383 residues; host buffers; synchronous.
+ */
+int msa_tile_bounds(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
+                    const int32_t *subst, int32_t gap, const int32_t *extents, int64_t *out_bounds);
+
 /* Thread-local description of the last failure in this thread ("" if none). */
 const char *msa_last_error(void);
 

@@ -384,6 +384,17 @@ extern "C" {
 
 int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_subst, int32_t gap,
                      msa_device_result *d_result, uint8_t *d_masks, void *stream) {
+    return msadp::run_plan(plan, d_residues, d_subst, gap, d_result, d_masks, stream, nullptr);
+}
+
+}  // extern "C"
+
+namespace msadp {
+
+// msa_plan_execute's steps; with `prune`, its kernels run between the encode
+// step and the fill (the plan's problem descriptor then points at prune->skip).
+int run_plan(msa_plan *plan, const char *d_residues, const int32_t *d_subst, int32_t gap, msa_device_result *d_result,
+             uint8_t *d_masks, void *stream, const PruneDesc *prune) {
     if (!plan || !d_subst || !d_result || (plan->hp.len_sum > 0 && (!d_residues || !d_masks)))
         return set_error(MSA_EINVAL, "NULL plan or device pointer");
     cudaStream_t s = (cudaStream_t)stream;
@@ -412,6 +423,10 @@ int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_su
     IODesc io{d_residues, d_subst, d_result, d_masks, gap, 0};
     e = launch_encode(plan->pp.prob, 1, plan->hp.len_sum, nullptr, io, s);
     if (e != cudaSuccess) return cuda_error(e, "encode launch");
+    if (prune) {
+        e = launch_prune(*prune, prune->greedy != 0, s);
+        if (e != cudaSuccess) return cuda_error(e, "pruning kernels");
+    }
     LaunchDesc L;
     memset(&L, 0, sizeof L);
     L.probs = plan->pp.prob;
@@ -445,6 +460,10 @@ int msa_plan_execute(msa_plan *plan, const char *d_residues, const int32_t *d_su
     }
     return MSA_OK;
 }
+
+}  // namespace msadp
+
+extern "C" {
 
 int msa_plan_timings(msa_plan *plan, float out_ms[3]) {
     if (!plan || !out_ms) return set_error(MSA_EINVAL, "NULL plan or output");
@@ -731,6 +750,202 @@ int msa_near_optimal(int k, const char *const *seqs, const int32_t *lens, const 
     cudaFree(d);
     msa_plan_destroy(plan);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Exact pruning: msa_align_pruned and msa_tile_bounds (host buffers).
+
+namespace {
+
+// Pruning descriptor for a plan's problem and tile extents E; returns the device
+// bytes its tables, rectangle maxima, bounds and flags need (laid out from `base`).
+size_t prune_layout(const HostPlan &hp, const int32_t *E, char *base, PruneDesc &D) {
+    memset(&D, 0, sizeof D);
+    const int k = hp.k;
+    D.k = k;
+    D.A = hp.A;
+    D.len_sum = hp.len_sum;
+    int32_t off = 0;
+    int64_t nt = 1;
+    for (int i = 0; i < k; ++i) {
+        D.len[i] = hp.lens[i];
+        D.cofs[i] = off;
+        off += hp.lens[i];
+        D.E[i] = E[i];
+        D.G[i] = (hp.rho[i] + E[i] - 1) / E[i];
+    }
+    for (int i = k - 1; i >= 0; --i) {
+        D.gstride[i] = nt;
+        nt *= D.G[i];
+    }
+    D.ntiles = nt;
+    int64_t toff = 0, boff = 0;
+    for (int i = 0; i < k; ++i)
+        for (int j = i + 1; j < k; ++j) {
+            D.pi[D.npairs] = i;
+            D.pj[D.npairs] = j;
+            D.toff[D.npairs] = toff;
+            D.boff[D.npairs] = boff;
+            toff += 2 * (int64_t)hp.rho[i] * hp.rho[j];
+            boff += (int64_t)D.G[i] * D.G[j];
+            ++D.npairs;
+        }
+    D.table_elems = toff;
+    D.nblocks = boff;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        char *p = base ? base + o : nullptr;
+        o = (o + bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    D.tables = reinterpret_cast<int32_t *>(take((size_t)toff * 4));
+    D.blk = reinterpret_cast<int64_t *>(take((size_t)boff * 8));
+    D.bound = reinterpret_cast<int64_t *>(take((size_t)nt * 8));
+    D.skip = reinterpret_cast<uint8_t *>(take((size_t)nt + 16));
+    D.lower = reinterpret_cast<int64_t *>(take(8));
+    D.stats = reinterpret_cast<int64_t *>(take(16));
+    return o;
+}
+
+// Shared set-up: request checks, a generic-tile-kernel plan, the pruning
+// descriptor, one device buffer holding inputs, outputs and the pruning arrays.
+struct PruneRun {
+    msa_plan *plan = nullptr;
+    char *d = nullptr;
+    PruneDesc D;
+    size_t o_res = 0, o_sub = 0, o_out = 0, o_masks = 0, o_prune = 0;
+    ~PruneRun() {
+        if (d) cudaFree(d);
+        if (plan) msa_plan_destroy(plan);
+    }
+};
+
+int prune_setup(int k, const char *const *seqs, const int32_t *lens, const char *alphabet, const int32_t *subst,
+                const int32_t *E, PruneRun &R) {
+    uint8_t amap[256];
+    int rc = validate_request(k, seqs, lens, alphabet, subst, amap);
+    if (rc) return rc;
+    for (int i = 0; i < k; ++i)
+        if (lens[i] > 16383) return set_error(MSA_ETOOBIG, "pruning takes sequences of at most 16383 residues");
+    rc = plan_create(k, lens, alphabet, kKernelTiles, -1, &R.plan);
+    if (rc) return rc;
+    const HostPlan &hp = R.plan->hp;
+    if (E)
+        for (int i = 0; i < k; ++i)
+            if (E[i] < 1) return set_error(MSA_EINVAL, "tile extent %d of axis %d is below 1", E[i], i);
+    const size_t pbytes = prune_layout(hp, E ? E : hp.E, nullptr, R.D);
+    const size_t total = (size_t)hp.len_sum, A = (size_t)hp.A;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return o;
+    };
+    R.o_res = take(total + 16);
+    R.o_sub = take(A * A * 4);
+    R.o_out = take(sizeof(msa_device_result));
+    R.o_masks = take(total + 16);
+    R.o_prune = take(pbytes);
+    cudaError_t e = cudaMalloc(&R.d, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        R.d = nullptr;
+        return set_error(MSA_ENOMEM, "pruning buffers: %s", cudaGetErrorString(e));
+    }
+    prune_layout(hp, E ? E : hp.E, R.d + R.o_prune, R.D);
+    R.D.codes = R.plan->pp.codes;
+    R.D.sub = reinterpret_cast<const int32_t *>(R.d + R.o_sub);
+    std::vector<char> res(total + 1);
+    size_t o = 0;
+    for (int i = 0; i < k; ++i) {
+        if (lens[i]) memcpy(res.data() + o, seqs[i], (size_t)lens[i]);
+        o += (size_t)lens[i];
+    }
+    e = cudaMemcpy(R.d + R.o_res, res.data(), total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(R.d + R.o_sub, subst, A * A * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(R.D.stats, 0, 16);
+    if (e != cudaSuccess) return cuda_error(e, "pruning inputs");
+    return MSA_OK;
+}
+
+}  // namespace
+
+int msa_align_pruned(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
+                     const int32_t *subst, int32_t gap, int32_t have_lower_bound, int64_t lower_bound,
+                     int32_t *out_score, char *out_alignment, msa_prune_stats *out_stats) {
+    if (!out_score || !out_alignment) return set_error(MSA_EINVAL, "NULL output pointer");
+    PruneRun R;
+    int rc = prune_setup(k, seqs, lens, alphabet, subst, nullptr, R);
+    if (rc) return rc;
+    const HostPlan &hp = R.plan->hp;
+    R.D.gap = gap;
+    R.D.greedy = have_lower_bound ? 0 : 1;
+    R.D.bound = nullptr;
+    cudaError_t e = cudaMemcpy(R.D.lower, &lower_bound, 8, cudaMemcpyHostToDevice);
+    // the fill reads the tiles' flags through the plan's problem descriptor
+    ProblemDesc pd;
+    fill_problem_desc(hp, R.plan->pp, 0, pd);
+    pd.skip = R.D.skip;
+    if (e == cudaSuccess) e = cudaMemcpy(R.plan->pp.prob, &pd, sizeof pd, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "pruning set-up");
+    cudaStream_t s = library_stream(&rc);
+    if (rc) return rc;
+    msa_device_result *d_res = reinterpret_cast<msa_device_result *>(R.d + R.o_out);
+    uint8_t *d_masks = reinterpret_cast<uint8_t *>(R.d + R.o_masks);
+    rc = run_plan(R.plan, R.d + R.o_res, R.D.sub, gap, d_res, d_masks, s, &R.D);
+    if (rc) return rc;
+    e = cudaStreamSynchronize(s);
+    msa_device_result res;
+    int64_t L = 0, st[2] = {0, 0};
+    std::vector<uint8_t> masks((size_t)hp.len_sum + 1);
+    if (e == cudaSuccess) e = cudaMemcpy(&res, d_res, sizeof res, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&L, R.D.lower, 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(st, R.D.stats, 16, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(masks.data(), d_masks, (size_t)hp.len_sum, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "pruning results");
+    // a bound above the optimum leaves out tiles of every optimal alignment: the
+    // corner is then unreachable or its best kept path scores below the bound
+    if (have_lower_bound && (res.status != MSA_OK || res.score < lower_bound))
+        return set_error(MSA_EINVAL, "lower bound %lld exceeds the optimum", (long long)lower_bound);
+    rc = status_error(res.status);
+    if (rc) return rc;
+    expand_alignment(k, seqs, lens, masks.data(), res.ncols, out_alignment);
+    *out_score = res.score;
+    if (out_stats) {
+        out_stats->lower_bound = L;
+        out_stats->tiles = hp.ntiles;
+        out_stats->tiles_skipped = st[0];
+        out_stats->cells_skipped = st[1];
+        out_stats->cells = hp.cells;
+    }
+    return MSA_OK;
+}
+
+int msa_tile_bounds(int k, const char *const *seqs, const int32_t *lens, const char *alphabet,
+                    const int32_t *subst, int32_t gap, const int32_t *extents, int64_t *out_bounds) {
+    if (!extents || !out_bounds) return set_error(MSA_EINVAL, "NULL extents or output");
+    PruneRun R;
+    int rc = prune_setup(k, seqs, lens, alphabet, subst, extents, R);
+    if (rc) return rc;
+    R.D.gap = gap;
+    R.D.greedy = 0;
+    R.D.skip = nullptr;
+    cudaStream_t s = library_stream(&rc);
+    if (rc) return rc;
+    IODesc io{R.d + R.o_res, R.D.sub, reinterpret_cast<msa_device_result *>(R.d + R.o_out),
+              reinterpret_cast<uint8_t *>(R.d + R.o_masks), gap, 0};
+    cudaError_t e = cudaMemsetAsync(R.plan->ws, 0, R.plan->reset_bytes, s);
+    if (e == cudaSuccess) e = launch_encode(R.plan->pp.prob, 1, R.plan->hp.len_sum, nullptr, io, s);
+    if (e == cudaSuccess) e = launch_prune(R.D, false, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    msa_device_result st;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, &R.plan->pp.state->istat, sizeof st, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "tile bounds");
+    rc = status_error(st.status);
+    if (rc) return rc;
+    e = cudaMemcpy(out_bounds, R.D.bound, (size_t)R.D.ntiles * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "tile bounds");
+    return MSA_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -63,6 +63,10 @@ size_t plan_layout(const HostPlan &hp, char *base, PlanPointers *pp, size_t *res
 void fill_problem_desc(const HostPlan &hp, const PlanPointers &pp, int64_t tile_base, ProblemDesc &d);
 int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t s);
 cudaError_t clear_faces(const HostPlan &hp, const PlanPointers &pp, cudaStream_t s = nullptr);
+// msa_plan_execute's steps, with the pruning kernels between encode and fill
+// when `prune` is given (msa_align_pruned).
+int run_plan(msa_plan *plan, const char *d_residues, const int32_t *d_subst, int32_t gap, msa_device_result *d_result,
+             uint8_t *d_masks, void *stream, const PruneDesc *prune);
 void expand_alignment(int k, const char *const *seqs, const int32_t *lens, const uint8_t *masks_rev,
                       int ncols, char *out);
 

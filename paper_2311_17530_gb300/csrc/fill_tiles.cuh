@@ -393,7 +393,36 @@ fill_tiles_kernel(const LaunchDesc L) {
             live = ld_volatile(&P.istat->status) == 0;
         else
             live = group_all<G>(grp, ld_volatile(&P.istat->status) == 0);
-        if (live) {
+        // A tile the pruning bound leaves out (its bound is below a lower bound on
+        // the optimum, so none of its cells lies on an optimal alignment) stores
+        // "no cell" scores for its successors and computes nothing; like every
+        // tile it waited for its face predecessors above and publishes below
+        // (its successors rely on its flag for their diagonal predecessors too).
+        // The flags are fixed before the fill, so the branch is the same for the
+        // whole group and holds no barrier.
+        const bool left_out = P.skip != nullptr && P.skip[lin] != 0;
+        if (live && left_out) {
+            int32_t *__restrict__ Qw = P.Q;
+            if constexpr (TM) {
+                int32_t *qb = Qw + lin * VOL;
+                for (int i = gl; i < VOL; i += TG) qb[i] = kNeg;
+            } else {
+                for (int i = gl; i < VOL; i += TG) {
+                    int r = i;
+                    bool in = true;
+                    int64_t gq = 0;
+#pragma unroll
+                    for (int j = 0; j < K; ++j) {
+                        const int cj = r / geo_st(K, E, j);
+                        r -= cj * geo_st(K, E, j);
+                        in = in && (cj < e[j]);
+                        gq += (int64_t)(o[j] + cj) * qstr[j];
+                    }
+                    if (in) Qw[gq] = kNeg;
+                }
+            }
+        }
+        if (live && !left_out) {
             const int A = P.A;
             const int32_t *__restrict__ tab = P.tab;
             const uint8_t *__restrict__ codes = P.codes;

@@ -69,6 +69,8 @@ struct ProblemDesc {
     uint8_t *tb;                 // traceback tensor
     int32_t *qcorner;            // packed key of the far corner
     msa_device_result *istat;    // internal status block (reset before every run)
+    const uint8_t *skip;         // generic tile kernel: per tile, nonzero = left out by the
+                                 // pruning bound (nullptr: every tile is filled)
 };
 
 // Per-execution inputs and outputs of one problem.
@@ -305,6 +307,33 @@ struct NearOut {
 };
 cudaError_t launch_near_optimal(const ProblemDesc *d_prob, IODesc io, int64_t delta, int32_t max_count, NearOut o,
                                 cudaStream_t s);
+
+// Exact pruning (prune.cu): the pairwise tables of every pair i < j, the largest
+// fwd + bwd of every tile rectangle, the tiles' bounds and, against a lower
+// bound L on the optimum, the tiles the fill leaves out. Device pointers:
+// tables (for pair pr at toff[pr]: fwd then bwd, (len_i + 1) x (len_j + 1) int32
+// each, row-major), blk (for pair pr at boff[pr]: G_i x G_j rectangle maxima),
+// bound (ntiles, optional), skip (ntiles flags, optional), lower (L: written by
+// the greedy walk, or set by the caller), stats ({tiles left out, their cells}).
+constexpr int kMaxPairs = MSA_MAX_K * (MSA_MAX_K - 1) / 2;
+struct PruneDesc {
+    int32_t k, A, gap, npairs, len_sum;
+    int32_t greedy;  // 1: L from the greedy walk; 0: *lower set by the caller
+    int32_t len[MSA_MAX_K], cofs[MSA_MAX_K], E[MSA_MAX_K], G[MSA_MAX_K];
+    int64_t gstride[MSA_MAX_K];
+    int32_t pi[kMaxPairs], pj[kMaxPairs];
+    int64_t toff[kMaxPairs], boff[kMaxPairs];
+    int64_t ntiles, nblocks, table_elems;
+    const uint8_t *codes;
+    const int32_t *sub;
+    int32_t *tables;
+    int64_t *blk;
+    int64_t *bound;
+    uint8_t *skip;
+    int64_t *lower;
+    int64_t *stats;
+};
+cudaError_t launch_prune(const PruneDesc &D, bool greedy, cudaStream_t s);
 cudaError_t launch_traceback(const ProblemDesc *d_probs, int nprob, const int32_t *err,
                              const IODesc *io_array, IODesc io_single, cudaStream_t s);
 

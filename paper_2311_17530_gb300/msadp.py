@@ -33,7 +33,12 @@ EXPORTED = ["msa_align", "msa_last_error", "msa_set_stream", "msa_config", "msa_
             "msa_cancel", "msa_drain", "msa_wave_sizes", "msa_tile_shape", "msa_version",
             "msa_plan_read_tb", "msa_plan_timings", "msa_align_noalloc", "msa_wait_any",
             "msa_set_tile_edge", "msa_get_tile_edge", "msa_set_line_segment", "msa_get_line_segment",
-            "msa_autotune", "msa_near_optimal"]
+            "msa_autotune", "msa_near_optimal", "msa_align_pruned", "msa_tile_bounds"]
+
+
+class PruneStats(ctypes.Structure):
+    _fields_ = [("lower_bound", ctypes.c_int64), ("tiles", ctypes.c_int64), ("tiles_skipped", ctypes.c_int64),
+                ("cells_skipped", ctypes.c_int64), ("cells", ctypes.c_int64)]
 
 
 class MsaError(RuntimeError):
@@ -85,6 +90,11 @@ def library() -> ctypes.CDLL:
     L.msa_near_optimal.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), i32p, ctypes.c_char_p, i32p,
                                    ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, i32p, i32p]
+    L.msa_align_pruned.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), i32p, ctypes.c_char_p, i32p,
+                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, i32p, ctypes.c_char_p,
+                                   ctypes.POINTER(PruneStats)]
+    L.msa_tile_bounds.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_char_p), i32p, ctypes.c_char_p, i32p,
+                                  ctypes.c_int32, i32p, ctypes.c_void_p]
     L.msa_last_error.restype = ctypes.c_char_p
     L.msa_version.restype = ctypes.c_char_p
     L.msa_set_stream.argtypes = [ctypes.c_void_p]
@@ -189,6 +199,40 @@ def msa_near_optimal(seqs: Sequence[str], alphabet: str, subst, gap: int, delta:
                     rows[i].append("-")
         out.append((int(scores[a]), ms, ["".join(r) for r in rows]))
     return out, bool(more.value)
+
+
+def msa_align_pruned(seqs: Sequence[str], alphabet: str, subst, gap: int,
+                     lower_bound: Optional[int] = None) -> Tuple[int, List[str], dict]:
+    """Optimal alignment with tiles below a lower bound left out (C-ABI call):
+    (score, rows, stats); lower_bound None lets the device build one."""
+    L = library()
+    k = len(seqs)
+    enc = [s.encode() for s in seqs]
+    arr = (ctypes.c_char_p * max(1, k))(*enc)
+    lens = _i32([len(s) for s in enc])
+    stride = sum(len(s) for s in enc) + 1
+    out = ctypes.create_string_buffer(k * stride)
+    score = ctypes.c_int32(0)
+    st = PruneStats()
+    _check(L.msa_align_pruned(k, arr, lens, alphabet.encode(), _table(subst), int(gap),
+                              0 if lower_bound is None else 1, int(lower_bound or 0), ctypes.byref(score), out,
+                              ctypes.byref(st)))
+    stats = {f: int(getattr(st, f)) for f, _ in PruneStats._fields_}
+    return int(score.value), _rows(out.raw, k, stride), stats
+
+
+def msa_tile_bounds(seqs: Sequence[str], alphabet: str, subst, gap: int, extents: Sequence[int]) -> np.ndarray:
+    """Every tile's pruning bound for these tile extents, computed on the device."""
+    L = library()
+    k = len(seqs)
+    enc = [s.encode() for s in seqs]
+    arr = (ctypes.c_char_p * max(1, k))(*enc)
+    lens = _i32([len(s) for s in enc])
+    grid = [-(-(len(s) + 1) // e) for s, e in zip(enc, extents)]
+    out = np.zeros(int(np.prod(grid)), dtype=np.int64)
+    _check(L.msa_tile_bounds(k, arr, lens, alphabet.encode(), _table(subst), int(gap), _i32(list(extents)),
+                             out.ctypes.data))
+    return out
 
 
 def msa_config(key: str, value: int) -> None:
