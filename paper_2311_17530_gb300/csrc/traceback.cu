@@ -524,6 +524,124 @@ __device__ void walk_tiles(const ProblemDesc &P, const IODesc &io, unsigned char
     }
 }
 
+// Line tiles spanning the whole last axis (layout 3 with one segment: the line
+// kernels' tiles of 32 lines over the first k - 1 axes, each a block of rows of
+// 32 bytes, cell (c, z) in row z + sum c_i at the lane of its line): a block is
+// too large to stage whole, so the CTA stages a window of rows of every tile
+// within a span below the current cell's tile along each line axis. A cell's
+// row never exceeds the current cell's z plus the block's largest skew and only
+// falls along a path, so the window holds rows [rhi - RW + 1, rhi] with rhi the
+// current z plus that skew, and thread 0 walks until a move leaves the staged
+// tiles or falls below the window. The spans grow the axis the walk would leave
+// soonest ((span - 1) x extent moves), within a staging volume that keeps a
+// re-stage short.
+constexpr int kLineWindowMinBlock = 2048;  // smaller line tiles are staged whole (walk_tiles)
+template <int K>
+__device__ void walk_lines(const ProblemDesc &P, const IODesc &io, unsigned char *smem, WalkState &ws) {
+    constexpr int NA = K - 1;
+    constexpr int RW = 40, RB = RW * 32;                // rows per window, bytes per staged tile
+    constexpr int kBudget = (24 * 1024) / RB;           // staged tiles (measured: 24 KB beats 48, 96, 192)
+    const int tid = threadIdx.x;
+    int E[NA], lst[NA], span[NA];
+    int skew = 0;
+    for (int i = 0; i < NA; ++i) {
+        E[i] = P.E[i];
+        lst[i] = P.lst[i];
+        span[i] = 1;
+        skew += E[i] - 1;
+    }
+    for (int guard = 0; guard < 64; ++guard) {
+        int n = 1, best = -1;
+        for (int i = 0; i < NA; ++i) n *= span[i];
+        for (int i = 0; i < NA; ++i)
+            if (n / span[i] * (span[i] + 1) <= kBudget && (best < 0 || span[i] * E[i] < span[best] * E[best]))
+                best = i;
+        if (best < 0) break;
+        ++span[best];
+    }
+    const int len_sum = P.len_sum;
+    while (true) {
+        __syncthreads();
+        if (ws.fail || at_origin(K, ws.x)) break;
+        int qlo[NA], sst[NA];
+        int n = 1;
+        for (int i = NA - 1; i >= 0; --i) {
+            const int q = ws.x[i] / E[i];
+            qlo[i] = max(0, q - span[i] + 1);
+            sst[i] = n;
+            n *= q - qlo[i] + 1;
+        }
+        const int rhi = ws.x[NA] + skew;
+        const int rlo = max(0, rhi - RW + 1);
+        const int nch = (rhi - rlo + 1) * 2;  // 16-byte chunks of a tile's window
+        for (int w = tid; w < n * nch; w += kTbThreads) {
+            const int sl = w / nch, ch = w - sl * nch;
+            int r = sl;
+            int64_t t = 0;
+            for (int i = 0; i < NA; ++i) {
+                const int d = r / sst[i];
+                r -= d * sst[i];
+                t += (int64_t)(qlo[i] + d) * P.gstride[i];
+            }
+            cp_async_16(smem + (size_t)sl * RB + 16 * ch, P.tb + t * P.tb_block + 32 * (int64_t)rlo + 16 * ch);
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (tid == 0) {
+            int x[K], c[NA], q[NA];
+            int sl = 0, loc = 32 * (ws.x[NA] - rlo);  // byte offset in the window: 32 (row - rlo) + lane
+            for (int i = 0; i < K; ++i) x[i] = ws.x[i];
+            for (int i = 0; i < NA; ++i) {
+                q[i] = x[i] / E[i];
+                c[i] = x[i] - q[i] * E[i];
+                loc += c[i] * lst[i];
+                sl += (q[i] - qlo[i]) * sst[i];
+            }
+            unsigned base = smem_u32(smem + (size_t)sl * RB);
+            int ncols = ws.ncols;
+            const int before = ncols;
+            bool fail = false;
+            while (!at_origin(K, x)) {
+                const int m = lds_u8(base + (unsigned)loc);
+                int zero = 0;
+                for (int i = 0; i < K; ++i) zero |= (x[i] == 0) << i;
+                if (m == 0 || (m >> K) != 0 || (m & zero) != 0 || ncols >= len_sum) {
+                    fail = true;
+                    break;
+                }
+                stg_u8(io.masks + ncols, m);
+                ++ncols;
+                bool out = false, cross = false;
+                if ((m >> NA) & 1) {
+                    --x[NA];
+                    loc -= 32;
+                }
+                for (int i = 0; i < NA; ++i)
+                    if ((m >> i) & 1) {
+                        --x[i];
+                        if (c[i] > 0) {
+                            --c[i];
+                            loc -= lst[i];
+                        } else {  // into the tile below along axis i
+                            c[i] = E[i] - 1;
+                            loc += (E[i] - 1) * lst[i];
+                            --q[i];
+                            sl -= sst[i];
+                            cross = true;
+                            out = out || q[i] < qlo[i];
+                        }
+                    }
+                if (out || loc < 0) break;  // left the staged tiles, or below the window's rows
+                if (cross) base = smem_u32(smem + (size_t)sl * RB);
+            }
+            if (ncols == before && !at_origin(K, x)) fail = true;  // a window must advance the walk
+            for (int i = 0; i < K; ++i) ws.x[i] = x[i];
+            ws.ncols = ncols;
+            if (fail) ws.fail = 1;
+        }
+    }
+}
+
 // Score of the recorded path, by the whole CTA: sum over columns of
 // u*|m| + sum over moved pairs (sub - 2 gap), each column at the position the
 // suffix of later moves (earlier in the record) gives it.
@@ -607,6 +725,12 @@ __global__ void __launch_bounds__(kTbThreads) traceback_kernel(const ProblemDesc
         walk_boxes<2>(P, io, smem, ws);
     else if (K == 3)
         walk_boxes<3>(P, io, smem, ws);
+    else if (P.tb_layout == 3 && P.G[K - 1] == 1 && P.tb_block > kLineWindowMinBlock && K == 4)
+        walk_lines<4>(P, io, smem, ws);
+    else if (P.tb_layout == 3 && P.G[K - 1] == 1 && P.tb_block > kLineWindowMinBlock && K == 5)
+        walk_lines<5>(P, io, smem, ws);
+    else if (P.tb_layout == 3 && P.G[K - 1] == 1 && P.tb_block > kLineWindowMinBlock && K == 6)
+        walk_lines<6>(P, io, smem, ws);
     else if (P.tb_layout >= 2 && K == 4)
         walk_tiles<4>(P, io, smem, ws);
     else if (P.tb_layout >= 2 && K == 5)
