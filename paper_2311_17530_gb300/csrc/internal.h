@@ -165,12 +165,12 @@ __host__ __device__ constexpr int line_skew_max(int K) {
 // Streamed line kernel (fill_lines_stream.cuh): a CTA of stream_warps(k) warps
 // sweeps a super-block of line blocks (each warp one 32-line block of the line
 // kernel, extents line_ext; the warps form a grid of extents stream_wg) over the
-// whole last axis in lockstep, in blocks of kStreamBlock steps; super-blocks
+// whole last axis in lockstep, in blocks of stream_block(k) steps; super-blocks
 // exchange faces as (value, epoch) entries indexed by time.
-constexpr int kStreamMinK = 4, kStreamMaxK = 5;
-constexpr int kStreamBlock = 8;  // steps per block = times per published face chunk
+constexpr int kStreamMinK = 4, kStreamMaxK = 6;
+__host__ __device__ constexpr int stream_block(int K) { return K == 6 ? 4 : 8; }  // steps per block = times per face chunk
 __host__ __device__ constexpr int stream_wg(int K, int i) {  // warps along line axis i
-    return K == 4 ? 2 : (i < 2 ? 2 : 1);                        // k = 4: 2 x 2 x 2; k = 5: 2 x 2 x 1 x 1
+    return K == 4 ? 2 : (i < 2 ? 2 : 1);  // k = 4: 2 x 2 x 2; k = 5: 2 x 2 x 1 x 1; k = 6: 2 x 2 x 1 x 1 x 1
 }
 __host__ __device__ constexpr int stream_warps(int K) {
     int w = 1;

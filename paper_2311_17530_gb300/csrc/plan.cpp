@@ -27,8 +27,8 @@ bool g_k3_tiles = false;
 bool g_k2_tiles = false;
 int g_line_z[MSA_MAX_K + 1] = {};            // 0: default segment
 bool g_lines_tiles[MSA_MAX_K + 1] = {};      // k = 4 .. 6: prefer the generic tile kernel
-constexpr bool kStreamDefault = true;        // the streamed form is the default at k = 4, 5
-bool g_stream[MSA_MAX_K + 1] = {false, false, false, false, kStreamDefault, kStreamDefault};
+constexpr bool stream_default(int k) { return k == 4 || k == 5; }  // where the streamed form is the default
+bool g_stream[MSA_MAX_K + 1] = {false, false, false, false, stream_default(4), stream_default(5), stream_default(6)};
 }  // namespace
 
 int tile_edge_for(int k) {
@@ -101,7 +101,7 @@ void set_prefer_stream(int k, bool v) {
     g_stream[k] = v;
 }
 
-void reset_prefer_stream(int k) { set_prefer_stream(k, kStreamDefault); }
+void reset_prefer_stream(int k) { set_prefer_stream(k, stream_default(k)); }
 
 bool stream_fits(int k, const int32_t *lens) {
     if (k < kStreamMinK || k > kStreamMaxK) return false;
@@ -234,12 +234,13 @@ bool score_and_traceback_layout(HostPlan &hp) {
         const int z = hp.E[k - 1];
         const bool stream = hp.kernel == kKernelStream;
         const int rows = z + line_skew_max(k);
-        hp.tb_block = (stream ? (rows + kStreamBlock - 1) / kStreamBlock * kStreamBlock : rows) * 32;
+        const int ub = stream_block(k);
+        hp.tb_block = (stream ? (rows + ub - 1) / ub * ub : rows) * 32;
         hp.lst[k - 1] = 32;
         for (int i = 0; i < k - 1; ++i) hp.lst[i] = 32 + line_lstride(k, i);
         // streamed: lzq times per face line (the whole sweep of a super-block),
         // stream_face_lines(k) lines per super-block
-        hp.lzq = stream ? (z + stream_skew_max(k) + kStreamBlock - 1) / kStreamBlock * kStreamBlock : (z + 3) / 4 * 4;
+        hp.lzq = stream ? (z + stream_skew_max(k) + ub - 1) / ub * ub : (z + 3) / 4 * 4;
         hp.qelems = stream ? hp.nunits * stream_face_lines(k) * hp.lzq * 2 : hp.ntiles * 32 * hp.lzq;
         hp.tb_layout = 3;
         hp.tb_dev_bytes = hp.ntiles * hp.tb_block;

@@ -53,13 +53,14 @@ def test_column_kernel_largest_alphabet(size, kernel):
     run_full(alphabet_problem(5100 + size, 3, [45, 37, 52], size), want_kernel=kernel)
 
 
-@pytest.mark.parametrize("kernel", [1, 4, 5])
-def test_largest_alphabet_generic_and_line_kernels(kernel):
-    """32 letters at k = 4 through the generic tile kernel (1), the line kernel (4)
-    and the streamed line kernel (5)."""
+@pytest.mark.parametrize("kernel,k,lens", [(1, 4, [13, 11, 14, 40]), (4, 4, [13, 11, 14, 40]),
+                                           (5, 4, [13, 11, 14, 40]), (5, 6, [5, 4, 3, 4, 3, 24])])
+def test_largest_alphabet_generic_and_line_kernels(kernel, k, lens):
+    """32 letters through the generic tile kernel (1), the line kernel (4) and the
+    streamed line kernel (5)."""
     msa.msa_config("fill_kernel", kernel)
     try:
-        run_full(alphabet_problem(5200, 4, [13, 11, 14, 40], 32), want_kernel=kernel)
+        run_full(alphabet_problem(5200 if k == 4 else 5200 + k, k, lens, 32), want_kernel=kernel)
     finally:
         msa.msa_config("fill_kernel", 0)
 

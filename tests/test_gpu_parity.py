@@ -112,11 +112,11 @@ def test_plan_reuse_is_deterministic():
 
 
 @pytest.mark.parametrize("name,kernel", [("pr1", 0), ("k2_protein", 0), ("k3_protein", 0), ("k4_dna", 4),
-                                         ("k4_dna", 5), ("k6_protein", 0)])
+                                         ("k4_dna", 5), ("k6_protein", 4), ("k6_protein", 5)])
 def test_full_size_workloads_against_stored_oracle_values(name, kernel):
     """Full-size workloads: score, alignment and sampled traceback bytes against
-    values written by tests/golden/make_golden.py (oracle only); k = 4 DNA through
-    both line kernels (segmented and streamed)."""
+    values written by tests/golden/make_golden.py (oracle only); k = 4 DNA and
+    k = 6 protein through both line kernels (segmented and streamed)."""
     path = os.path.join(GOLDEN, f"{name}.json")
     if not os.path.exists(path):
         pytest.skip(f"{path} not generated")
@@ -237,7 +237,8 @@ def test_k3_auto_picks_column_kernel():
 
 @pytest.mark.parametrize("kernel,k,lens", [(2, 3, [40, 37, 45]), (2, 3, [63, 95, 70]), (3, 2, [150, 170]),
                                            (3, 2, [33, 400]), (4, 4, [9, 13, 10, 40]), (1, 4, [9, 13, 10, 40]),
-                                           (5, 4, [9, 13, 10, 40]), (5, 5, [5, 4, 5, 9, 40])])
+                                           (5, 4, [9, 13, 10, 40]), (5, 5, [5, 4, 5, 9, 40]),
+                                           (5, 6, [5, 4, 3, 3, 2, 20])])
 def test_every_fill_kernel_records_the_corner_key(kernel, k, lens):
     """Every fill kernel records the far corner's packed key; the traceback
     compares the rescored path with it. A consistent result (status 0, the
@@ -259,7 +260,8 @@ def test_every_fill_kernel_records_the_corner_key(kernel, k, lens):
 @pytest.mark.parametrize("seed", [3, 99])
 @pytest.mark.parametrize("kernel,k,lens", [(2, 3, [70, 65, 90]), (3, 2, [150, 170]), (1, 3, [30, 25, 28]),
                                            (1, 4, [9, 8, 10, 7]), (1, 5, [5, 4, 6, 5, 4]),
-                                           (5, 4, [9, 13, 10, 70]), (5, 5, [5, 4, 5, 9, 40])])
+                                           (5, 4, [9, 13, 10, 70]), (5, 5, [5, 4, 5, 9, 40]),
+                                           (5, 6, [5, 4, 3, 3, 2, 20])])
 def test_shuffled_orders_over_a_poisoned_traceback(kernel, k, lens, seed):
     """Tickets permuted inside every wave (another topological order of the same
     tiles or columns) and the traceback tensor filled with 0xFF before the fill:

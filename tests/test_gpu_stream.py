@@ -1,4 +1,4 @@
-"""The streamed line fill (k = 4, 5; one warp per 32-line block over the whole last
+"""The streamed line fill (k = 4..6; one warp per 32-line block over the whole last
 axis, faces published as (value, epoch) entries) against the oracle, bit for
 bit: shapes spanning several line blocks with ragged tails and several 8-step
 blocks of the last axis, degenerate shapes, the ties-heavy scheme, other
@@ -17,11 +17,13 @@ from paper_2311_17530_gb300 import msadp
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-# line blocks are 2x4x4 (k=4) and 2x2x2x4 (k=5); the last axis spans several
-# 8-position chunks with a ragged tail
+# line blocks are 2x4x4 (k=4), 2x2x2x4 (k=5) and 2x2x2x2x2 (k=6), super-blocks
+# 4x8x8, 4x4x2x4 and 4x4x2x2x2 lines; the last axis spans several 8-position
+# chunks with a ragged tail
 SHAPES = [
     (4, [9, 13, 10, 30]), (4, [9, 13, 10, 70]), (4, [3, 7, 9, 129]), (4, [17, 5, 6, 17]),
     (5, [5, 4, 5, 9, 40]), (5, [3, 4, 3, 9, 70]), (5, [4, 2, 5, 3, 23]),
+    (6, [5, 4, 3, 3, 2, 20]), (6, [3, 5, 2, 4, 3, 9]), (6, [8, 4, 2, 2, 4, 33]),
 ]
 
 
@@ -73,6 +75,8 @@ def test_shapes_match_oracle(k, lens):
     (4, [0, 0, 0, 0]), (4, [1, 1, 1, 1]), (4, [0, 5, 3, 9]), (4, [6, 0, 0, 40]), (4, [2, 4, 4, 0]),
     (4, [1, 3, 3, 7]), (4, [2, 4, 4, 8]), (4, [3, 5, 5, 15]), (4, [12, 2, 1, 16]), (4, [1, 1, 1, 200]),
     (5, [0, 1, 0, 1, 0]), (5, [1, 1, 1, 3, 15]), (5, [2, 2, 2, 4, 31]), (5, [4, 3, 2, 1, 0]),
+    (6, [0, 1, 0, 1, 0, 1]), (6, [1, 1, 1, 1, 1, 15]), (6, [3, 3, 1, 1, 1, 7]), (6, [4, 4, 2, 2, 2, 8]),
+    (6, [2, 0, 3, 1, 2, 0]),
 ])
 def test_degenerate_and_block_boundary_shapes(k, lens):
     check(inputs.random_problem(7100 + sum(lens) + 7 * k, k, lens, alphabet=inputs.PROTEIN))
@@ -82,7 +86,7 @@ def test_ties_heavy_scoring_scheme():
     """The paper's +1/0/-1/0 scheme (section 5.2): many equal candidates, so the
     lowest-mask rule decides most cells."""
     table = np.eye(4, dtype=np.int32)
-    for k, lens in [(4, [9, 8, 10, 40]), (5, [4, 5, 3, 6, 20])]:
+    for k, lens in [(4, [9, 8, 10, 40]), (5, [4, 5, 3, 6, 20]), (6, [3, 4, 2, 3, 2, 17])]:
         check(inputs.random_problem(7200 + k, k, lens, table=table, gap=-1))
 
 
@@ -91,7 +95,7 @@ def test_shuffled_column_orders(seed):
     """Tickets permuted inside every wave: another topological order of the same
     columns, so a missing dependency shows up as a different traceback byte."""
     msa.msa_config("test_shuffle_waves", seed)
-    for k, lens in [(4, [9, 13, 10, 70]), (5, [5, 4, 5, 9, 40])]:
+    for k, lens in [(4, [9, 13, 10, 70]), (5, [5, 4, 5, 9, 40]), (6, [5, 4, 3, 3, 2, 20])]:
         check(inputs.random_problem(7300 + seed + k, k, lens, alphabet=inputs.PROTEIN, related=True))
 
 
@@ -99,7 +103,7 @@ def test_every_cell_written_over_a_poisoned_buffer():
     """The traceback tensor is filled with 0xFF before the fill; no cell of the
     tensor may keep it (0xFF is no valid move for k < 8) and all equal the oracle."""
     msa.msa_config("test_poison_tb", 1)
-    for k, lens in [(4, [9, 13, 10, 70]), (5, [3, 4, 3, 9, 70])]:
+    for k, lens in [(4, [9, 13, 10, 70]), (5, [3, 4, 3, 9, 70]), (6, [3, 5, 2, 4, 3, 9])]:
         p = inputs.random_problem(7400 + k, k, lens, alphabet=inputs.DNA)
         score, rows, status, tb, info = run(p)
         assert status == 0
