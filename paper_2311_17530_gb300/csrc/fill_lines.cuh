@@ -87,12 +87,13 @@ __host__ __device__ constexpr int line_v_words() {
     for (int i = 0; i < K - 1; ++i) top += line_ext(K, i) * line_stride(K, Z, i);
     return round_up(top + 4, 4);
 }
-// Pair-table row stride: at least Z, and congruent to skew_max + 1 mod 32, so that
-// lanes reading row c_i at position t - sum c hit distinct banks unless they read
-// the same word.
+// Pair-table row stride: at least Z + skew_max (a lane reads its row at positions
+// -skew_max .. Z + skew_max - 1, unclamped, in the sweep), and congruent to
+// skew_max + 1 mod 32, so that lanes reading row c_i at position t - sum c hit
+// distinct banks unless they read the same word.
 template <int K, int Z>
 __host__ __device__ constexpr int line_pt_stride() {
-    int s = Z;
+    int s = Z + line_skew_max(K);
     while (s % 32 != (line_skew_max(K) + 1) % 32) ++s;
     return s;
 }
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(line_best_warps<K, Z>() * 32) fill_lines_kerne
     constexpr int ZS = line_pt_stride<K, Z>();
     constexpr int MASKB = (1 << K) - 1;
     constexpr int NW = line_best_warps<K, Z>();
+    static_assert(line_cta_fixed_bytes<K>() >= 4 * SMAX, "sweep reads below the first box stay in shared memory");
 
     extern __shared__ __align__(16) unsigned char smem[];
     // per CTA: one entry per halo'd line, halo lines first, then the 32 lines of
@@ -356,7 +358,9 @@ __global__ void __launch_bounds__(line_best_warps<K, Z>() * 32) fill_lines_kerne
                         if (below && src >= 0) zf[u] = __ldcg(Qg + (src - gsz) * QB + (int)((e >> 14) & 31) * ZQ + (Ez - 1));
                     }
                 }
-                constexpr int HB = K >= 6 ? 8 : 16;  // loads in flight per lane (registers bound it at k = 6)
+                // loads in flight per lane: two batches at k = 6 (registers, not shared
+                // memory, would bound the warps of the shorter segment at 24)
+                constexpr int HB = K >= 6 && Z > 16 ? 24 : 16;
                 for (int i0 = 0; i0 < NH * NQ; i0 += 32 * HB) {
                     int4 val[HB];
                     int dst[HB];
@@ -394,8 +398,12 @@ __global__ void __launch_bounds__(line_best_warps<K, Z>() * 32) fill_lines_kerne
             }
             __syncwarp();
 
-            // The sweep. Lanes outside their segment (z < 0 or z >= Zt) compute on
-            // clamped positions and store nothing but their traceback byte slot.
+            // The sweep. Every lane reads its own skewed position, in range or not,
+            // so the 32 loads of a step stay in 32 banks: at z = -1 word 0 holds the
+            // position below; the words read at z < -1 (up to skew_max - 1 words
+            // before the box, inside the CTA's shared memory) and at z >= Zt feed
+            // only candidates that are overwritten or never stored, and the
+            // traceback byte such a lane writes is a padding byte of the tile.
             const bool origin_lane = lin == 0 && lane == 0;
             int Wl = (z0 - skew) * (1 << NA);  // W(x) = Wl + ts * 2^NA at step ts
 #pragma unroll
@@ -418,12 +426,11 @@ __global__ void __launch_bounds__(line_best_warps<K, Z>() * 32) fill_lines_kerne
             for (int ts = 0; ts < nsteps; ++ts) {
                 const int z = ts - skew;
                 const bool act = (unsigned)z < (unsigned)Zt;
-                const int zz = z < 0 ? 0 : (z >= Zt ? Zt : z + 1);  // clamped word offset
+                const int zz = z + 1;  // word offset of position z
                 const int32_t *vp = V + vbase + zz;
-                const int zp = zz > 0 ? zz - 1 : 0;  // clamped position for the pair tables
                 int p[NA];
 #pragma unroll
-                for (int i = 0; i < NA; ++i) p[i] = PT[ptoff[i] + zp];
+                for (int i = 0; i < NA; ++i) p[i] = PT[ptoff[i] + z];
                 int T[M + 1];
                 T[0] = 0;
 #pragma unroll
