@@ -192,6 +192,9 @@ __host__ __device__ constexpr int stream_face_lines(int K) {  // lines of a supe
     return all - inner;
 }
 
+// k = 2 band kernel: rows per lane (a band is 32 of them per lane, 32 lanes).
+constexpr int kBand2RowsPerLane = 2;
+
 // k = 3 column kernel geometry (shared by the planner and the kernel).
 //
 // A CTA owns a column: rows x0 in [A*WR, A*WR + WR) (warp w holds rows

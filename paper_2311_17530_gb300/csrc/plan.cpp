@@ -131,8 +131,8 @@ void tile_extents(int k, const int32_t *lens, int kernel, int edge, int32_t *E) 
         E[2] = lens[2] + 1;
         return;
     }
-    if (kernel == kKernelBand2) {  // bands of 32 rows spanning every column
-        E[0] = 32;
+    if (kernel == kKernelBand2) {  // bands of 32 lanes x kBand2RowsPerLane rows spanning every column
+        E[0] = 32 * kBand2RowsPerLane;
         E[1] = lens[1] + 1;
         return;
     }
@@ -346,8 +346,9 @@ int plan_shape(int k, const int32_t *lens, int A, int kernel_choice, HostPlan &h
         return MSA_ETOOBIG;
     }
     if (hp.kernel == kKernelBand2) {
-        // scores: only each band's last row, the face the band below reads
-        hp.face0_stride = round_up64(hp.rho[1], 32);
+        // scores: only each band's last row, the face the band below reads, as
+        // (value, tag) entries of two words
+        hp.face0_stride = 2 * round_up64(hp.rho[1], 32);
         hp.qelems = hp.ntiles * hp.face0_stride;
     }
 

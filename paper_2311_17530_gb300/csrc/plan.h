@@ -22,7 +22,7 @@ enum FillKernel {
 
 // Kernels whose faces carry (value, epoch) entries: the plan clears them before
 // the first launch and gives every launch a new epoch.
-inline bool tagged_faces(int kernel) { return kernel == kKernelCol3 || kernel == kKernelStream; }
+inline bool tagged_faces(int kernel) { return kernel == kKernelCol3 || kernel == kKernelStream || kernel == kKernelBand2; }
 
 struct HostPlan {
     int k = 0;

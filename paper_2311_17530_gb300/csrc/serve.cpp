@@ -500,8 +500,8 @@ int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg
             size_t rb = 0;
             plan_layout(r->hp, arena_base_ + r->ws_off, &pp, &rb);
             fill_problem_desc(r->hp, pp, tile_base, hdesc[i]);
-            hdesc[i].clear_faces = r->hp.kernel == kKernelCol3 ? 1 : 0;
-            clear = clear || r->hp.kernel == kKernelCol3;
+            hdesc[i].clear_faces = tagged_faces(r->hp.kernel) ? 1 : 0;
+            clear = clear || tagged_faces(r->hp.kernel);
             tile_base += r->hp.ntiles;
             hdesc[i].amap = reinterpret_cast<uint8_t *>(D + off_amap + (size_t)i * 256);
             hdesc[i].istat = distat + i;
@@ -534,10 +534,10 @@ int Server::launch(Slot &sl, std::vector<ServeReq *> &batch, const Settings &cfg
                                                         (long long)g.tickets);
         g.grid = persistent_grid(g.k, g.kernel, g.tickets, g.maxA, g.edge);  // no occupancy query in a capture
     }
-    bool col3 = false;
-    for (const Group &g : groups) col3 = col3 || g.kernel == kKernelCol3;
+    bool tagged = false;
+    for (const Group &g : groups) tagged = tagged || tagged_faces(g.kernel);
     cudaStream_t s = sl.s;
-    if (col3) {
+    if (tagged) {
         if (epoch_ >= 32767) {
             // tags (epoch << 16) + T would repeat: clear every face the arena may hold
             for (auto &o : slots_)
