@@ -155,7 +155,7 @@ KERNEL_SOURCES = {
     "fill_lines": ["csrc/fill_lines.cuh"] + [f"csrc/fill_lines_k{k}.cu" for k in range(4, 7)] +
                   ["csrc/internal.h", "csrc/device_common.cuh", "../include/msadp.h"],
     "fill_lines_stream": ["csrc/fill_lines_stream.cuh", "csrc/fill_lines.cuh"] +
-                         [f"csrc/fill_stream_k{k}.cu" for k in range(4, 6)] +
+                         [f"csrc/fill_stream_k{k}.cu" for k in range(4, 7)] +
                          ["csrc/internal.h", "csrc/device_common.cuh", "../include/msadp.h"],
 }
 

@@ -42,8 +42,8 @@
 namespace msadp {
 namespace {
 
-constexpr int kBandWarps = 4;  // warps per CTA, one band each (one per scheduler)
 constexpr int kBandR = kBand2RowsPerLane;
+constexpr int kBandWarps = kBandR <= 2 ? 4 : 2;  // warps per CTA, one band each (the tables take 32 KB)
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
     unsigned long long v;
@@ -114,18 +114,23 @@ __global__ void __launch_bounds__(kBandWarps * 32) fill_band2_kernel(const Launc
         int cblk = 0;        // lane c holds the residue code consumed at column 32 * block + c
         int bj = 0;          // the code consumed at this lane's column (shifted along the lanes)
         bool ok = true;
+        // the next block's codes, loaded a block ahead (the face is loaded when the
+        // block starts: loading it earlier, while the band above still writes it,
+        // measured slower)
+        int cnext = (lane >= 1 && lane < rho1) ? (int)c1[lane - 1] : 0;
 
         // One step; CHECK: some lane may be off the columns [0, rho1).
         auto step = [&](int s, auto check) {
             constexpr bool CHECK = decltype(check)::value;
             if ((s & 31) == 0 && s < rho1) {  // lane 0 enters block s / 32: stage its codes and face
                 const int col = s + lane;
-                cblk = (col >= 1 && col < rho1) ? (int)c1[col - 1] : 0;
+                cblk = cnext;
+                cnext = (col + 32 < rho1) ? (int)c1[col + 31] : 0;
                 if (band > 0) {
                     uint64_t t0 = 0;
+                    unsigned long long e = 0;
+                    if (col < rho1) e = ld_relaxed_u64(face_in + col);
                     for (int polls = 0;; ++polls) {
-                        unsigned long long e = 0;
-                        if (col < rho1) e = ld_relaxed_u64(face_in + col);
                         const bool good = col >= rho1 || (int)(e >> 32) == epoch;
                         fblk = col < rho1 ? (int)(unsigned)e : kNeg;
                         if (__all_sync(kFull, good)) break;
@@ -139,6 +144,7 @@ __global__ void __launch_bounds__(kBandWarps * 32) fill_band2_kernel(const Launc
                             return;
                         }
                         __nanosleep(polls < 16 ? 32 : 256);
+                        if (col < rho1) e = ld_relaxed_u64(face_in + col);
                     }
                 }
             }
@@ -156,11 +162,18 @@ __global__ void __launch_bounds__(kBandWarps * 32) fill_band2_kernel(const Launc
             const bool valid = !CHECK || (unsigned)j < (unsigned)rho1;
             const int w = i0 + 2 * j;  // W(x) of row i0
             const int *tr = trow + bj * R * 32 + lane;
+            // the left and diagonal candidates do not depend on the row above: only
+            // the max with the cell above, and forming the key, are chained over q
+            int x[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                x[q] = __viaddmax_s32(diag, tr[q * 32], prev[q]);
+                diag = prev[q];
+            }
             unsigned m4[R];
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                const int left = prev[q];
-                int acc = __viaddmax_s32(diag, tr[q * 32], max(up, left));
+                const int acc = max(up, x[q]);
                 int m = (w + q - acc) & 3;
                 int v = acc + m;
                 if (CHECK && origin_lane && q == 0 && j == 0) {  // H(0) = 0: no move
@@ -168,7 +181,6 @@ __global__ void __launch_bounds__(kBandWarps * 32) fill_band2_kernel(const Launc
                     m = 0;
                 }
                 m4[q] = (unsigned)m;
-                diag = left;
                 up = v;
                 if (valid) prev[q] = v;
             }

@@ -193,7 +193,7 @@ __host__ __device__ constexpr int stream_face_lines(int K) {  // lines of a supe
 }
 
 // k = 2 band kernel: rows per lane (a band is 32 of them per lane, 32 lanes).
-constexpr int kBand2RowsPerLane = 2;
+constexpr int kBand2RowsPerLane = 4;
 
 // k = 3 column kernel geometry (shared by the planner and the kernel).
 //

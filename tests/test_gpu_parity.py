@@ -215,8 +215,9 @@ def test_k2_tile_and_band_kernels_boundaries(kernel):
 
 
 def test_k2_band_wait_timeout_is_reported_not_hung():
-    """A withheld band never publishes its face, so the band below times out."""
-    p = inputs.random_problem(7, 2, [100, 80])
+    """A withheld band never publishes its face, so the band below times out
+    (three bands of 128 rows)."""
+    p = inputs.random_problem(7, 2, [300, 80])
     with msa.Plan(2, p.lens, p.alphabet) as plan:
         assert plan.info().fill_kernel == 3
     msa.msa_config("spin_timeout_ms", 200)
