@@ -144,6 +144,8 @@ def time_oracle(p, target_cells: float):
     return q, dt
 
 
+WIDE_Z = 25  # the longest last axis the streamed kernel's whole-column form (k = 6) holds
+
 # Source files each fill kernel is compiled from (its own file and the headers it includes).
 KERNEL_SOURCES = {
     "fill_col3": ["csrc/fill_col3.cu", "csrc/api_internal.h", "csrc/plan.h", "csrc/internal.h",
@@ -154,6 +156,8 @@ KERNEL_SOURCES = {
                    "csrc/device_common.cuh", "../include/msadp.h"],
     "fill_lines": ["csrc/fill_lines.cuh"] + [f"csrc/fill_lines_k{k}.cu" for k in range(4, 7)] +
                   ["csrc/internal.h", "csrc/device_common.cuh", "../include/msadp.h"],
+    "fill_lines_wide": ["csrc/fill_lines_wide.cuh", "csrc/fill_stream_k6.cu", "csrc/internal.h",
+                        "csrc/device_common.cuh", "../include/msadp.h"],
     "fill_lines_stream": ["csrc/fill_lines_stream.cuh", "csrc/fill_lines.cuh"] +
                          [f"csrc/fill_stream_k{k}.cu" for k in range(4, 7)] +
                          ["csrc/internal.h", "csrc/device_common.cuh", "../include/msadp.h"],
@@ -513,6 +517,8 @@ def measure_workload(name, steps, warmup, args, dist, dev, sms, world, rank, clo
 
     kernel = {1: "fill_tiles", 2: "fill_col3", 3: "fill_band2", 4: "fill_lines",
               5: "fill_lines_stream"}[int(info.fill_kernel)]
+    if kernel == "fill_lines_stream" and p.k == 6 and p.lens[-1] + 1 <= WIDE_Z:
+        kernel = "fill_lines_wide"  # the streamed kernel's whole-column form
     ops = alg_ops_per_cell(p.k) * p.cells
     achieved = ops / (fill_ms / 1e3) / 1e12
     peak = alu_peak_tiops(sms)

@@ -243,7 +243,7 @@ int launch_fill(const HostPlan &hp, const LaunchDesc &L, int grid, cudaStream_t 
     cudaError_t e = hp.kernel == kKernelCol3    ? launch_fill_col3(L, grid, col3_smem_bytes(hp.A), s)
                   : hp.kernel == kKernelBand2 ? launch_fill_band2(L, grid, s)
                   : hp.kernel == kKernelLines ? launch_fill_lines(hp.k, hp.edge, L, grid, s)
-                  : hp.kernel == kKernelStream ? launch_fill_stream(hp.k, L, grid, s)
+                  : hp.kernel == kKernelStream ? launch_fill_stream(hp.k, L, grid, s, hp.rho[hp.k - 1])
                                               : launch_fill_tiles(hp.k, hp.edge, L, grid, s);
     return e == cudaSuccess ? MSA_OK : cuda_error(e, "fill kernel launch");
 }

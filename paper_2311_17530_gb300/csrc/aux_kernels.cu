@@ -173,15 +173,15 @@ int fill_lines_warps_per_cta(int k, int z) {
 
 cudaError_t launch_fill_stream_k4(const LaunchDesc &L, int grid, cudaStream_t s);
 cudaError_t launch_fill_stream_k5(const LaunchDesc &L, int grid, cudaStream_t s);
-cudaError_t launch_fill_stream_k6(const LaunchDesc &L, int grid, cudaStream_t s);
+cudaError_t launch_fill_stream_k6(const LaunchDesc &L, int grid, cudaStream_t s, int rho_s);
 int fill_stream_ctas_k4();
 int fill_stream_ctas_k5();
 int fill_stream_ctas_k6();
 
-cudaError_t launch_fill_stream(int k, const LaunchDesc &L, int grid, cudaStream_t s) {
+cudaError_t launch_fill_stream(int k, const LaunchDesc &L, int grid, cudaStream_t s, int rho_s) {
     return k == 4   ? launch_fill_stream_k4(L, grid, s)
            : k == 5 ? launch_fill_stream_k5(L, grid, s)
-           : k == 6 ? launch_fill_stream_k6(L, grid, s)
+           : k == 6 ? launch_fill_stream_k6(L, grid, s, rho_s)
                     : cudaErrorInvalidValue;
 }
 

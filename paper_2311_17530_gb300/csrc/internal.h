@@ -169,6 +169,9 @@ __host__ __device__ constexpr int line_skew_max(int K) {
 // exchange faces as (value, epoch) entries indexed by time.
 constexpr int kStreamMinK = 4, kStreamMaxK = 6;
 __host__ __device__ constexpr int stream_block(int K) { return K == 6 ? 4 : 8; }  // steps per block = times per face chunk
+// k = 6: the streamed kernel's whole-column form (fill_lines_wide.cuh) holds a
+// last axis of at most kWideZ positions; longer ones take the pipelined form.
+constexpr int kWideZ = 25;
 __host__ __device__ constexpr int stream_wg(int K, int i) {  // warps along line axis i
     return K == 4 ? 2 : (i < 2 ? 2 : 1);  // k = 4: 2 x 2 x 2; k = 5: 2 x 2 x 1 x 1; k = 6: 2 x 2 x 1 x 1 x 1
 }
@@ -290,7 +293,7 @@ cudaError_t launch_fill_band2(const LaunchDesc &L, int grid, cudaStream_t s);
 cudaError_t launch_fill_lines(int k, int z, const LaunchDesc &L, int grid, cudaStream_t s);
 int fill_lines_ctas_per_sm(int k, int z);
 int fill_lines_warps_per_cta(int k, int z);
-cudaError_t launch_fill_stream(int k, const LaunchDesc &L, int grid, cudaStream_t s);
+cudaError_t launch_fill_stream(int k, const LaunchDesc &L, int grid, cudaStream_t s, int rho_s);  // rho_s: last axis
 int fill_stream_ctas_per_sm(int k);
 int fill_band2_ctas_per_sm();
 int fill_band2_warps_per_cta();

@@ -27,7 +27,7 @@ bool g_k3_tiles = false;
 bool g_k2_tiles = false;
 int g_line_z[MSA_MAX_K + 1] = {};            // 0: default segment
 bool g_lines_tiles[MSA_MAX_K + 1] = {};      // k = 4 .. 6: prefer the generic tile kernel
-constexpr bool stream_default(int k) { return k == 4 || k == 5; }  // where the streamed form is the default
+constexpr bool stream_default(int k) { return k >= 4 && k <= 6; }  // where the streamed form is the default
 bool g_stream[MSA_MAX_K + 1] = {false, false, false, false, stream_default(4), stream_default(5), stream_default(6)};
 }  // namespace
 
@@ -116,7 +116,10 @@ int choose_kernel(int k, const int32_t *lens, int A, int requested, bool allow_s
     if (requested == kKernelStream && k >= kStreamMinK && k <= kStreamMaxK) return kKernelStream;
     if (k >= kLinesMinK && k <= kLinesMaxK &&
         (requested == kKernelLines || requested == kKernelStream || (requested == kKernelAuto && !prefer_tiles_lines(k)))) {
-        if (requested == kKernelAuto && allow_stream && prefer_stream(k) && stream_fits(k, lens)) return kKernelStream;
+        // at k = 6 only the whole-column form (last axis of at most kWideZ) beats the line kernel
+        if (requested == kKernelAuto && allow_stream && prefer_stream(k) && stream_fits(k, lens) &&
+            (k != 6 || lens[k - 1] + 1 <= kWideZ))
+            return kKernelStream;
         return kKernelLines;
     }
     if (k == 2 && (requested == kKernelBand2 || (requested == kKernelAuto && !prefer_tiles_k2()))) return kKernelBand2;

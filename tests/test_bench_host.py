@@ -84,3 +84,11 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0"], capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_whole_column_limit_matches_the_library():
+    """bench.py names the k = 6 whole-column kernel by the same last-axis limit
+    the planner and the kernel use."""
+    src = open(os.path.join(ROOT, "paper_2311_17530_gb300", "csrc", "internal.h")).read()
+    assert f"constexpr int kWideZ = {bench.WIDE_Z};" in src
+    assert len(bench.kernel_source_digest("fill_lines_wide")) == 16

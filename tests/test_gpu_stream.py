@@ -141,14 +141,17 @@ def test_withheld_column_times_out_not_hangs():
 
 
 def test_automatic_choice_and_serving():
-    """k = 4, 5 plans take the streamed kernel by default; serving runs the
-    segmented line kernel for the same shapes and matches the oracle."""
+    """k = 4, 5 plans take the streamed kernel by default, k = 6 plans when the
+    last axis fits the whole-column form; serving runs the segmented line kernel
+    for the same shapes and matches the oracle."""
     msa.msa_config("fill_kernel", 0)
     for k in (4, 5, 6):
         msa.msa_set_line_segment(k, 0)  # default choices
     with msa.Plan(4, [9, 13, 10, 70], inputs.DNA) as plan:
         assert plan.info().fill_kernel == 5
-    with msa.Plan(6, [3, 4, 3, 4, 3, 12], inputs.DNA) as plan:
+    with msa.Plan(6, [3, 4, 3, 4, 3, 12], inputs.DNA) as plan:  # the whole-column form fits
+        assert plan.info().fill_kernel == 5
+    with msa.Plan(6, [3, 4, 3, 4, 3, 30], inputs.DNA) as plan:  # it does not: the line kernel
         assert plan.info().fill_kernel == 4
     for choice in (0, 5):
         msa.msa_config("fill_kernel", choice)
