@@ -111,14 +111,16 @@ def test_every_cell_written_over_a_poisoned_buffer():
         check(p)
 
 
-def test_back_to_back_executions_take_only_this_launchs_entries():
+@pytest.mark.parametrize("k,lens", [(4, [9, 13, 10, 70]), (6, [5, 4, 3, 3, 2, 20])])
+def test_back_to_back_executions_take_only_this_launchs_entries(k, lens):
     """One plan executed on different inputs of the same shape, several times in a
-    row: each launch's faces carry a new epoch, so a consumer that took an entry
-    of the previous launch (a stale score) would disagree with the oracle."""
-    lens = [9, 13, 10, 70]
-    probs = [inputs.random_problem(7500 + i, 4, lens, alphabet=inputs.PROTEIN, related=i % 2 == 0)
+    row: each launch's faces carry a new epoch (k = 4) or are read only after this
+    launch's completion flags, zeroed at every launch (k = 6, whole-column form),
+    so a consumer that took a face of the previous launch (a stale score) would
+    disagree with the oracle."""
+    probs = [inputs.random_problem(7500 + 10 * k + i, k, lens, alphabet=inputs.PROTEIN, related=i % 2 == 0)
              for i in range(4)]
-    plan = msa.Plan(4, lens, inputs.PROTEIN)
+    plan = msa.Plan(k, lens, inputs.PROTEIN)
     try:
         for p in probs + probs[:2]:
             check(p, plan)
@@ -126,10 +128,12 @@ def test_back_to_back_executions_take_only_this_launchs_entries():
         plan.close()
 
 
-def test_withheld_column_times_out_not_hangs():
-    """A withheld column publishes its faces with tag 0, which no launch uses, so
-    its consumers give up after the wait limit and the plan reports a timeout."""
-    p = inputs.random_problem(7600, 4, [9, 13, 10, 70])
+@pytest.mark.parametrize("k,lens", [(4, [9, 13, 10, 70]), (6, [5, 4, 3, 3, 2, 20]), (6, [3, 4, 2, 3, 2, 30])])
+def test_withheld_column_times_out_not_hangs(k, lens):
+    """A withheld column publishes nothing valid (its faces carry tag 0, or its
+    completion flag is never set), so its consumers give up after the wait limit
+    and the plan reports a timeout; the next execution is whole again."""
+    p = inputs.random_problem(7600 + k + lens[-1], k, lens)
     msa.msa_config("spin_timeout_ms", 200)
     msa.msa_config("test_withhold_tile", 0)
     try:
