@@ -169,9 +169,12 @@ int msa_set_stream(void *stream);
  *                       request, in arrival order (default 1)
  *   "fill_kernel"       0: automatic; 1: generic tile kernel; 2: k=3 column kernel;
  *                       3: k=2 band kernel; 4: k=4..6 line kernel (segments of the
- *                       last axis); 5: k=4,5 streamed line kernel (one warp per block of
- *                       32 lines over the whole last axis; k=6 takes 4). The automatic
- *                       choice at k=4,5 is 5 (until msa_autotune picks otherwise); the
+ *                       last axis); 5: k=4..6 streamed line kernel (a CTA sweeps a
+ *                       super-block of 32-line blocks over the whole last axis; at
+ *                       k=6 the whole-column form when the last axis holds at most
+ *                       25 positions, the pipelined form otherwise). The automatic
+ *                       choice is 5 at k=4,5 and at k=6 for a last axis of at most 25
+ *                       positions, else 4 (until msa_autotune picks otherwise); the
  *                       serving loop runs 4 where 5 would be chosen or asked for
  *   "timing"            1: msa_plan_execute records per-stage CUDA events (default 0)
  *   "verify_corner"     1: later plans and requests on the k=3 column kernel record the
@@ -209,7 +212,7 @@ typedef struct msa_plan_info {
     int64_t tiles;
     int32_t waves;              /* tile hyperplanes (section 3.1, Eq. 2) */
     int32_t fill_kernel;        /* 1 generic tile kernel, 2 k=3 column kernel, 3 k=2 band kernel,
-                                   4 k=4..6 line kernel, 5 k=4,5 streamed line kernel */
+                                   4 k=4..6 line kernel, 5 k=4..6 streamed line kernel */
     void   *d_tb;               /* device pointer of the uint8 traceback tensor: row-major with
                                    tb_strides for the tile kernel (k <= 3) and the band kernel;
                                    tile-major for the tile kernel at k >= 4 and for the line
@@ -375,7 +378,8 @@ int msa_get_tile_edge(int k, int32_t *out_edge);
  * sweeps; the planner cuts the axis into equal segments no longer than this.
  * Only compiled lengths are accepted (k=4: 8 16 32; k=5: 16 32; k=6: 16 25); 0
  * restores the default (32, 32, 25) and the automatic choice of the line kernel
- * for k = 4..6 (its streamed form at k = 4, 5). Later plans and serving batches
+ * for k = 4..6 (its streamed form at k = 4, 5, and at k = 6 for a last axis of at
+ * most 25 positions). Later plans and serving batches
  * use the setting (the streamed form has no segments). Host-only, thread-safe;
  * MSA_EINVAL for other k or lengths.
  */
@@ -402,7 +406,7 @@ typedef struct msa_tuning {
 /*
  * Time every compiled tile edge for k (and the column kernel for k = 3, the band
  * kernel for k = 2, each compiled line segment for k = 4..6 and the streamed line
- * kernel for k = 4, 5) on a synthetic problem with these lengths over an alphabet
+ * kernel for k = 4..6) on a synthetic problem with these lengths over an alphabet
  * of alphabet_size letters: one warm-up and `repeats` executions each, on the
  * library stream. The fastest becomes the choice for k (msa_set_tile_edge or
  * msa_set_line_segment, and whether the automatic kernel choice takes the band,
