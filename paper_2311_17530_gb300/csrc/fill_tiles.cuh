@@ -6,7 +6,9 @@
 // handed out by an atomic ticket in wave order (tiles of equal index sum: the
 // partitions section 3 groups by their distance from the origin); a tile starts once
 // its k face predecessors have published completion (bounded acquire waits),
-// which also covers every edge and corner predecessor transitively.
+// which also covers every edge and corner predecessor transitively (in a pruned
+// fill, where left-out tiles wait for nothing, a live tile waits for every lower
+// neighbour directly).
 //
 // One warp (two for a few large shapes, see tiles_group) fills one tile in
 // shared memory: the halo comes from the score scratch in global memory (L2,
@@ -376,12 +378,33 @@ fill_tiles_kernel(const LaunchDesc L) {
         }
         const int64_t tile_base = P.tile_base;
 
-        // Wait for the face predecessors (one thread per axis).
+        // Wait for the face predecessors (one thread per axis); their own waits
+        // make every lower neighbour complete. In a pruned fill (P.skip set) a
+        // tile the bound leaves out waits for nothing -- it only stores "no cell"
+        // scores -- so that chain is broken: a live tile there waits for every
+        // lower neighbour it reads (one thread per nonempty subset of the axes).
+        // The flags are fixed before the fill, so the branch is the same for the
+        // whole group.
+        const bool left_out = P.skip != nullptr && P.skip[lin] != 0;
         bool ok = true;
+        if (P.skip == nullptr) {
 #pragma unroll
-        for (int j = 0; j < K; ++j)
-            if (gl == j && tco[j] > 0)
-                ok = wait_at_least(&L.done[tile_base + lin - P.gstride[j]], 1, L.err, L.spin_ns);
+            for (int j = 0; j < K; ++j)
+                if (gl == j && tco[j] > 0)
+                    ok = wait_at_least(&L.done[tile_base + lin - P.gstride[j]], 1, L.err, L.spin_ns);
+        } else if (!left_out) {
+            for (int S = gl + 1; S < (1 << K) && ok; S += TG) {
+                bool in = true;
+                int64_t n = lin;
+#pragma unroll
+                for (int j = 0; j < K; ++j)
+                    if ((S >> j) & 1) {
+                        in = in && tco[j] > 0;
+                        n -= P.gstride[j];
+                    }
+                if (in) ok = wait_at_least(&L.done[tile_base + n], 1, L.err, L.spin_ns);
+            }
+        }
         if (!group_all<G>(grp, ok)) {
             if (gl == 0) atomicCAS(L.err, 0, MSA_ETIMEOUT);
             break;
@@ -395,12 +418,8 @@ fill_tiles_kernel(const LaunchDesc L) {
             live = group_all<G>(grp, ld_volatile(&P.istat->status) == 0);
         // A tile the pruning bound leaves out (its bound is below a lower bound on
         // the optimum, so none of its cells lies on an optimal alignment) stores
-        // "no cell" scores for its successors and computes nothing; like every
-        // tile it waited for its face predecessors above and publishes below
-        // (its successors rely on its flag for their diagonal predecessors too).
-        // The flags are fixed before the fill, so the branch is the same for the
-        // whole group and holds no barrier.
-        const bool left_out = P.skip != nullptr && P.skip[lin] != 0;
+        // "no cell" scores for its successors, computes nothing and publishes
+        // below. The branch is the same for the whole group and holds no barrier.
         if (live && left_out) {
             int32_t *__restrict__ Qw = P.Q;
             if constexpr (TM) {
