@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(stream_threads<K>(), stream_min_ctas<K>()) fil
     uint32_t *ftab = reinterpret_cast<uint32_t *>(sm + LY::FTAB);  // face lines: ring base
     int32_t *nb = sm + LY::NB;
     int32_t *crow = sm + LY::CROW;
-    volatile int32_t *misc = sm + LY::MISC;  // [0] ticket, [1] prefetch verdict, [2] poll verdict
+    // [0] ticket, [2] poll verdict, [3] / [4] the two count checkpoints' verdicts
+    volatile int32_t *misc = sm + LY::MISC;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     if (tid == 0) {
@@ -561,9 +562,11 @@ __global__ void __launch_bounds__(stream_threads<K>(), stream_min_ctas<K>()) fil
 
         // One block of U steps, unrolled: PAR = b mod NPAR makes every ring slot a
         // constant.
-        // Warp 0 judges the counts at steps J1 and J2, every thread reads the
-        // verdict after that step's barrier and issues the next chunk's copies.
+        // Warp 0 judges the counts at steps J1 and J2 (each verdict in its own
+        // word), every thread reads a verdict after that step's barrier and
+        // issues the next chunk's copies.
         constexpr int J1 = U / 4, J2 = U / 2 + U / 8;
+        static_assert(J1 < J2 && J2 + 1 < U, "checkpoints");
         auto block = [&](int b, auto par) {
             constexpr int PAR = decltype(par)::value;
             const bool want = b + 1 < nblk;  // the next block needs chunk b + 1
@@ -582,11 +585,11 @@ __global__ void __launch_bounds__(stream_threads<K>(), stream_min_ctas<K>()) fil
             auto step = [&](int s) {
                 if ((s == J1 || s == J2) && want && !issued && warp == 0) {
                     const bool r = __all_sync(kFull, my_src < 0 || count_ok(cnt, b + 1));
-                    if (lane == 0) misc[1] = r;
+                    if (lane == 0) misc[s == J1 ? 3 : 4] = r;
                     if (!r && my_src >= 0) cnt = ld_relaxed(prog + my_src);
                 }
                 if ((s == J1 + 1 || s == J2 + 1) && want && !issued) {
-                    issued = misc[1] != 0;
+                    issued = misc[s == J1 + 1 ? 3 : 4] != 0;
                     if (issued) halo_issue(b + 1, true);
                 }
                 if (s == U / 2 - 1 && refill) pt_entries();
