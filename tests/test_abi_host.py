@@ -104,3 +104,17 @@ def test_wave_shuffle_hook_is_validated_and_keeps_plans_valid():
         assert all(g >= 1 for g in grid)
     finally:
         msa.msa_config("test_shuffle_waves", 0)
+
+
+def test_automatic_kernel_choice_by_k_and_last_axis():
+    """The planner's automatic choice, read through the tile shape it reports: the
+    streamed line kernel sweeps the whole last axis in one tile (k = 4, 5, and at
+    k = 6 only while the whole-column form holds the axis: 25 positions), the line
+    kernel cuts it into equal segments (k = 6 beyond 25 positions: at most 25, the
+    compiled length not above it)."""
+    for lens in ([9, 13, 10, 70], [4, 5, 3, 6, 40], [5, 4, 3, 3, 2, 20], [5, 4, 3, 3, 2, 24]):
+        ext, grid = msa.msa_tile_shape(lens)
+        assert ext[-1] == lens[-1] + 1 and grid[-1] == 1, lens
+    for lens in ([5, 4, 3, 3, 2, 25], [5, 4, 3, 3, 2, 30], [3, 3, 3, 3, 3, 60]):
+        ext, grid = msa.msa_tile_shape(lens)
+        assert ext[-1] <= 25 and grid[-1] >= 2 and ext[-1] * grid[-1] >= lens[-1] + 1, lens
