@@ -394,7 +394,7 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic", "config": {"workload": p.name, "k": p.k, "lens": p.lens, "cells": p.cells},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -531,7 +531,7 @@ def measure_workload(name, steps, warmup, args, dist, dev, sms, world, rank, clo
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         q, dt = time_oracle(p, cpu_cells if cpu_cells is not None else PER_WORKLOAD_CPU_CELLS.get(name, 2e7))
-        cpu = {"value": q.cells / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": q.cells / dt, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
                "sample": f"oracle on prefixes {q.lens} of {p.name} ({q.cells} cells, {dt:.1f} s)"}
     out = {"value": value, "unit": UNIT, "steps": steps, "warmup": warmup, "ms_per_step": ms_step,
            "config": {"workload": p.name, "k": p.k, "lens": p.lens, "cells": p.cells, "tiles": int(info.tiles),
